@@ -1,0 +1,148 @@
+/*
+ * zm.h -- C ABI of the GB300 Z-Model velocity library (libzm.so).
+ *
+ * The library evaluates the hot path of the Z-Model Rayleigh-Taylor interface solver that
+ * Beatnik (arXiv:2406.05490) exercises, on one GPU:
+ *   - the surface-derivative stencils, two nodes deep, with periodic or free-edge ghosts
+ *     (paper Sec. 3.1, SurfaceMesh and BoundaryCondition);
+ *   - the exact all-pairs desingularised Birkhoff-Rott velocity (Sec. 2 BRSolver and
+ *     Sec. 3.2.1 ExactBRSolver, the "high order" model);
+ *   - the FFT Riesz-transform velocity (Sec. 2, the "low order" model);
+ *   - the vorticity derivative and third-order Runge-Kutta time integration, three derivative
+ *     evaluations per step (Sec. 3.1 ZModel and TimeIntegrator).
+ *
+ * Equations (the paper names these ingredients but prints no formulas; this is the reading
+ * the library implements).  Mesh n1 x n2, parameter alpha = (i dx1, j dx2), dx_l = L_l / n_l,
+ * node p = i*n2 + j.  Per node z = (z1, z2, z3) and w = (w1, w2).
+ *     a_l = D_l z (4th-order central), h_kl = a_k . a_l, det = h11 h22 - h12^2,
+ *     N = a1 x a2 / |a1 x a2|,  gamma = w1 a2 - w2 a1,
+ *     high order:  u_i = -(dx1 dx2 / 4 pi) sum_j (z_i - z_j) x gamma_j / (|z_i - z_j|^2 + delta^2)^(3/2)
+ *     low order:   u = -1/2 (R1 w1 + R2 w2) N,   R_l^(k) = -i k_l / |k|  (0 at k = 0, Nyquist)
+ *     Phi = g z3 + 1/8 (h22 w1^2 - 2 h12 w1 w2 + h11 w2^2) / det + 1/2 |u|^2
+ *     dz/dt = u,    dw_l/dt = -2 A D_l Phi + mu (D_1^2 + D_2^2) w_l
+ *     SSP-RK3: y1 = y + dt L(y); y2 = 3/4 y + 1/4 (y1 + dt L(y1)); y' = 1/3 y + 2/3 (y2 + dt L(y2)).
+ *
+ * Layout of every field array: FP64, component-major, z[c * N + p] (c = 0..2), w[c * N + p]
+ * (c = 0..1), u[c * N + p], wdot[c * N + p], with N = n1 * n2.
+ *
+ * Pointers: every array argument may be host memory or device memory of the context's GPU;
+ * the library tells them apart with cudaPointerGetAttributes.  Caller pointers are borrowed
+ * for the duration of the call only.  With host pointers a call completes before it returns;
+ * with device pointers it is asynchronous on the context's stream (see zm_set_stream).
+ *
+ * Errors: every int-returning call returns ZM_OK (0) or a negative ZM_ERR_* code;
+ * zm_last_error() returns a per-thread message describing the most recent failure.
+ * Threading: calls on one context are not re-entrant; distinct contexts may be used from
+ * distinct threads and streams concurrently.
+ */
+#ifndef ZM_H
+#define ZM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define ZM_OK 0
+#define ZM_ERR_INVALID (-1)      /* bad argument (null pointer, size, parameter range)       */
+#define ZM_ERR_NOMEM (-2)        /* device or host allocation failed                          */
+#define ZM_ERR_CUDA (-3)         /* a CUDA runtime call or kernel launch failed               */
+#define ZM_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up (status word set)      */
+#define ZM_ERR_UNSUPPORTED (-5)  /* valid but not supported: low order on a free-edge mesh,
+                                    FFT side not a power of two, medium order              */
+#define ZM_ERR_NONFINITE (-6)    /* the state became NaN/Inf (checked by zm_check_finite)    */
+#define ZM_ERR_BUSY (-7)         /* resource budget exhausted (serving admission)            */
+
+/* model order (paper Sec. 3.1, ZModel order tag) and precision flag OR'ed into it */
+#define ZM_ORDER_LOW 0
+#define ZM_ORDER_MEDIUM 1
+#define ZM_ORDER_HIGH 2
+#define ZM_PREC_FP64 0x000
+#define ZM_PREC_FP32C 0x100 /* BR pair terms in FP32 (hi/lo positions), per-tile FP32 partials,
+                               FP64 accumulation across tiles; everything else FP64 */
+
+typedef struct {
+    int32_t n1, n2;   /* nodes along alpha1 (slow index i) and alpha2 (fast index j), >= 5 */
+    double L1, L2;    /* parameter-domain lengths (> 0); dx_l = L_l / n_l                 */
+    int32_t periodic; /* 1: periodic ghosts, z1/z2 shifted by L1/L2 across the seam;
+                         0: free edges, two ghost nodes by linear extrapolation            */
+} zm_mesh;
+
+typedef struct zm_ctx zm_ctx;
+
+/* Create a context for one interface on the current CUDA device.  Allocates all device state
+ * and workspace (owned by the context until zm_destroy).  delta > 0 is the Birkhoff-Rott core
+ * size (high order); mu >= 0 the artificial viscosity; `order` is ZM_ORDER_* | ZM_PREC_*.
+ * Returns ZM_ERR_UNSUPPORTED for low order on a free-edge mesh or a non power-of-two side,
+ * and for medium order. */
+int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double delta, int order,
+              zm_ctx **out);
+
+/* Use `cuda_stream` (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL for
+ * the legacy default stream) for all later work of this context. */
+int zm_set_stream(zm_ctx *ctx, void *cuda_stream);
+
+/* Copy a state (z: 3N doubles, w: 2N doubles) into the context's resident state. */
+int zm_set_state(zm_ctx *ctx, const double *z, const double *w);
+
+/* Copy the resident state out (either pointer may be NULL to skip it). */
+int zm_get_state(zm_ctx *ctx, double *z, double *w);
+
+/* One derivative evaluation L(z, w) = (u, wdot) without advancing the state (one ZModel call,
+ * paper Sec. 3.1).  z, w: input state, or both NULL to use the resident state.
+ * u: 3N velocity output (dz/dt).  wdot: 2N vorticity derivative output, may be NULL. */
+int zm_velocity(zm_ctx *ctx, const double *z, const double *w, double *u, double *wdot);
+
+/* Advance the resident state by nsteps SSP-RK3 steps of size dt (three derivative evaluations
+ * per step, paper Sec. 3.1 TimeIntegrator).  Asynchronous on the context's stream. */
+int zm_step(zm_ctx *ctx, double dt, int nsteps);
+
+/* Wait for the context's stream; reports ZM_ERR_TIMEOUT / ZM_ERR_CUDA raised by its kernels. */
+int zm_sync(zm_ctx *ctx);
+
+/* Free the context and all device memory it owns (synchronises its stream first). */
+void zm_destroy(zm_ctx *ctx);
+
+/* Static description of a status code, and the calling thread's last detailed message. */
+const char *zm_error_string(int code);
+const char *zm_last_error(void);
+
+/* ---- instrumentation ------------------------------------------------------------------- */
+
+/* Kernel classes timed by the optional per-context CUDA-event profiler. */
+#define ZM_K_GEOMETRY 0 /* ghost fill + tangents + normal + sheet-strength records          */
+#define ZM_K_BR 1       /* all-pairs Birkhoff-Rott sum                                      */
+#define ZM_K_REDUCE 2   /* split-source reduction + Phi                                     */
+#define ZM_K_VORT 3     /* grad Phi, Laplacian, vorticity derivative, RK3 combine           */
+#define ZM_K_FFT 4      /* Riesz-transform FFT passes                                       */
+#define ZM_K_COUNT 5
+
+typedef struct {
+    double ms[ZM_K_COUNT];        /* summed CUDA-event time per kernel class               */
+    int64_t launches[ZM_K_COUNT]; /* launches per kernel class                             */
+    int64_t pairs;                /* Birkhoff-Rott pair interactions evaluated (N^2 each)  */
+} zm_profile;
+
+/* Turn event timing around every launch on (1) or off (0); turning it on clears counters.
+ * Counting launches and pairs is always on. */
+int zm_set_profiling(zm_ctx *ctx, int on);
+/* Synchronises the stream and reports counters accumulated since the last reset. */
+int zm_get_profile(zm_ctx *ctx, zm_profile *out);
+int zm_reset_profile(zm_ctx *ctx);
+
+/* Check the resident state for NaN/Inf: returns ZM_OK or ZM_ERR_NONFINITE (synchronous). */
+int zm_check_finite(zm_ctx *ctx);
+
+/* Measure a CUDA-core throughput of the current GPU with CUDA events (the roofline denominator
+ * of the Birkhoff-Rott kernels; the paper has no counterpart).  kind 0: FP32 FMA flop/s (FMA =
+ * 2 flops), 1: FP64 FMA flop/s, 2: MUFU rsqrt operations/s.  Synchronous; allocates 64 bytes. */
+int zm_measure_peak(int kind, double *ops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZM_H */

@@ -1,0 +1,392 @@
+// zm_api.cu -- the C ABI of libzm.so (declared and documented in include/zm.h): context
+// lifecycle, argument checks, host/device pointer handling, and the orchestration of one
+// derivative evaluation (paper Sec. 3.1 ZModel) and of SSP-RK3 steps (Sec. 3.1 TimeIntegrator).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "zm_internal.cuh"
+
+namespace zm {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_check(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return ZM_OK;
+    return set_error(ZM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---- profiling ------------------------------------------------------------------------------
+
+static void prof_fold(zm_ctx *c)
+{
+    if (c->ev_live.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto &e : c->ev_live) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) c->prof.ms[e.cls] += ms;
+        c->ev_pool.push_back(e.a);
+        c->ev_pool.push_back(e.b);
+    }
+    c->ev_live.clear();
+}
+
+static cudaEvent_t prof_event(zm_ctx *c)
+{
+    if (c->ev_pool.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+}
+
+void prof_begin(zm_ctx *c, int cls, cudaEvent_t *a)
+{
+    c->prof.launches[cls] += 1;
+    *a = nullptr;
+    if (!c->profiling) return;
+    if (c->ev_live.size() >= 4096) prof_fold(c);
+    *a = prof_event(c);
+    if (*a) cudaEventRecord(*a, c->stream);
+}
+
+void prof_end(zm_ctx *c, int cls, cudaEvent_t a)
+{
+    if (!c->profiling || !a) return;
+    cudaEvent_t b = prof_event(c);
+    if (!b) return;
+    cudaEventRecord(b, c->stream);
+    c->ev_live.push_back({cls, a, b});
+}
+
+// ---- derivative ---------------------------------------------------------------------------------
+
+// One evaluation of L(y): after it, c->u holds dz/dt and c->phi holds Phi.
+int derivative(zm_ctx *c, const double *y)
+{
+    int rc = launch_geometry(c, y);
+    if (rc) return rc;
+    if (c->order == ZM_ORDER_LOW) return launch_riesz(c, y);
+    rc = launch_br(c, y);
+    if (rc) return rc;
+    return launch_reduce(c);
+}
+
+static bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int copy_in(zm_ctx *c, double *dst, const double *src, size_t count)
+{
+    const cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    return cuda_check(cudaMemcpyAsync(dst, src, count * sizeof(double), k, c->stream), "copy in");
+}
+
+static int copy_out(zm_ctx *c, double *dst, const double *src, size_t count, bool *to_host)
+{
+    const bool dev = is_device_ptr(dst);
+    if (!dev) *to_host = true;
+    const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    return cuda_check(cudaMemcpyAsync(dst, src, count * sizeof(double), k, c->stream), "copy out");
+}
+
+static int read_status(zm_ctx *c)
+{
+    int h = 0;
+    int rc = cuda_check(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                        "status read");
+    if (rc) return rc;
+    rc = cuda_check(cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (rc) return rc;
+    if (h & kErrTimeout) {
+        cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+        return set_error(ZM_ERR_TIMEOUT, "a bounded device-side wait gave up (status word set)");
+    }
+    return ZM_OK;
+}
+
+}  // namespace zm
+
+using namespace zm;
+
+extern "C" {
+
+const char *zm_error_string(int code)
+{
+    switch (code) {
+    case ZM_OK: return "ok";
+    case ZM_ERR_INVALID: return "invalid argument";
+    case ZM_ERR_NOMEM: return "out of memory";
+    case ZM_ERR_CUDA: return "CUDA error";
+    case ZM_ERR_TIMEOUT: return "device-side wait timed out";
+    case ZM_ERR_UNSUPPORTED: return "unsupported configuration";
+    case ZM_ERR_NONFINITE: return "state is not finite";
+    case ZM_ERR_BUSY: return "resource budget exhausted";
+    default: return "unknown status";
+    }
+}
+
+const char *zm_last_error(void) { return g_last_error.c_str(); }
+
+static bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+void zm_destroy(zm_ctx *c)
+{
+    if (!c) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto &e : c->ev_live) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    void *bufs[] = {c->y0, c->ya, c->yb, c->u, c->phi, c->q, c->nrm, c->src, c->part,
+                    c->fa, c->fb, c->tw1, c->tw2, c->err, c->flag};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete c;
+}
+
+int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double delta, int order,
+              zm_ctx **out)
+{
+    if (!mesh || !out) return set_error(ZM_ERR_INVALID, "zm_create: null mesh or out pointer");
+    *out = nullptr;
+    const int ord = order & 0xff;
+    const int fp32c = (order & ZM_PREC_FP32C) ? 1 : 0;
+    if ((order & ~(0xff | ZM_PREC_FP32C)) != 0 || ord > ZM_ORDER_HIGH)
+        return set_error(ZM_ERR_INVALID, "zm_create: unknown order/precision flags");
+    if (mesh->n1 < 5 || mesh->n2 < 5 || (int64_t)mesh->n1 * mesh->n2 > (1 << 26))
+        return set_error(ZM_ERR_INVALID, "zm_create: mesh sides must be >= 5 and n1*n2 <= 2^26");
+    if (!(mesh->L1 > 0) || !(mesh->L2 > 0) || !std::isfinite(mesh->L1) || !std::isfinite(mesh->L2))
+        return set_error(ZM_ERR_INVALID, "zm_create: L1, L2 must be finite and > 0");
+    if (!std::isfinite(atwood) || !std::isfinite(g) || !(mu >= 0) || !std::isfinite(mu))
+        return set_error(ZM_ERR_INVALID, "zm_create: atwood, g must be finite and mu >= 0");
+    if (ord == ZM_ORDER_HIGH && !(delta > 0 && std::isfinite(delta)))
+        return set_error(ZM_ERR_INVALID, "zm_create: the Birkhoff-Rott core size delta must be > 0");
+    if (ord == ZM_ORDER_MEDIUM)
+        return set_error(ZM_ERR_UNSUPPORTED, "zm_create: medium order is not implemented");
+    if (ord == ZM_ORDER_LOW && !mesh->periodic)
+        return set_error(ZM_ERR_UNSUPPORTED,
+                         "zm_create: low order needs a periodic mesh (periodic FFT solver)");
+    if (ord == ZM_ORDER_LOW && (!pow2(mesh->n1) || !pow2(mesh->n2) || mesh->n1 > 4096 ||
+                                mesh->n2 > 4096 || mesh->n1 < 8 || mesh->n2 < 8))
+        return set_error(ZM_ERR_UNSUPPORTED,
+                         "zm_create: low order needs power-of-two sides in [8, 4096]");
+
+    zm_ctx *c = new (std::nothrow) zm_ctx();
+    if (!c) return set_error(ZM_ERR_NOMEM, "zm_create: host allocation failed");
+    c->mesh = *mesh;
+    c->atwood = atwood;
+    c->g = g;
+    c->mu = mu;
+    c->delta = delta;
+    c->order = ord;
+    c->fp32c = fp32c;
+    c->stream = nullptr;
+    cudaGetDevice(&c->device);
+    Geom &G = c->geom;
+    G.n1 = mesh->n1;
+    G.n2 = mesh->n2;
+    G.N = mesh->n1 * mesh->n2;
+    G.L1 = mesh->L1;
+    G.L2 = mesh->L2;
+    G.dx1 = mesh->L1 / mesh->n1;
+    G.dx2 = mesh->L2 / mesh->n2;
+    G.periodic = mesh->periodic ? 1 : 0;
+    const size_t N = G.N;
+
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+
+    auto alloc = [&](void **p, size_t bytes) -> bool {
+        if (cudaMalloc(p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    };
+    bool ok = alloc((void **)&c->y0, 5 * N * sizeof(double)) &&
+              alloc((void **)&c->ya, 5 * N * sizeof(double)) &&
+              alloc((void **)&c->yb, 5 * N * sizeof(double)) &&
+              alloc((void **)&c->u, 3 * N * sizeof(double)) &&
+              alloc((void **)&c->phi, N * sizeof(double)) &&
+              alloc((void **)&c->q, N * sizeof(double)) && alloc((void **)&c->err, sizeof(int)) &&
+              alloc((void **)&c->flag, sizeof(int));
+    if (ok && ord == ZM_ORDER_HIGH) {
+        c->tiling = make_tiling(G);
+        c->plan = plan_br(G, c->tiling, fp32c, sms);
+        const size_t rec = fp32c ? kRec32 * sizeof(float) : kRec64 * sizeof(double);
+        c->src_bytes = (size_t)c->tiling.ntiles * c->tiling.ts * rec;
+        ok = alloc(&c->src, c->src_bytes) &&
+             alloc((void **)&c->part, (size_t)c->plan.nsplit * 3 * N * sizeof(double));
+        // padding slots of edge tiles stay zero for good: zero strength, no contribution
+        if (ok) ok = cudaMemset(c->src, 0, c->src_bytes) == cudaSuccess;
+    }
+    if (ok && ord == ZM_ORDER_LOW) ok = alloc((void **)&c->nrm, 3 * N * sizeof(double));
+    if (ok) ok = cudaMemset(c->err, 0, sizeof(int)) == cudaSuccess &&
+                 cudaMemset(c->y0, 0, 5 * N * sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        zm_destroy(c);
+        return set_error(ZM_ERR_NOMEM, "zm_create: device allocation failed");
+    }
+    if (ord == ZM_ORDER_LOW) {
+        int rc = fft_setup(c);
+        if (rc) {
+            zm_destroy(c);
+            return rc;
+        }
+    }
+    int rc = cuda_check(cudaDeviceSynchronize(), "zm_create");
+    if (rc) {
+        zm_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return ZM_OK;
+}
+
+int zm_set_stream(zm_ctx *c, void *stream)
+{
+    if (!c) return set_error(ZM_ERR_INVALID, "zm_set_stream: null context");
+    c->stream = static_cast<cudaStream_t>(stream);
+    return ZM_OK;
+}
+
+int zm_set_state(zm_ctx *c, const double *z, const double *w)
+{
+    if (!c || !z || !w) return set_error(ZM_ERR_INVALID, "zm_set_state: null argument");
+    const size_t N = c->geom.N;
+    int rc = copy_in(c, c->y0, z, 3 * N);
+    if (!rc) rc = copy_in(c, c->y0 + 3 * N, w, 2 * N);
+    if (!rc && (!is_device_ptr(z) || !is_device_ptr(w)))
+        rc = cuda_check(cudaStreamSynchronize(c->stream), "zm_set_state");
+    return rc;
+}
+
+int zm_get_state(zm_ctx *c, double *z, double *w)
+{
+    if (!c) return set_error(ZM_ERR_INVALID, "zm_get_state: null context");
+    const size_t N = c->geom.N;
+    bool host = false;
+    int rc = ZM_OK;
+    if (z) rc = copy_out(c, z, c->y0, 3 * N, &host);
+    if (!rc && w) rc = copy_out(c, w, c->y0 + 3 * N, 2 * N, &host);
+    if (!rc && host) rc = read_status(c);
+    return rc;
+}
+
+int zm_velocity(zm_ctx *c, const double *z, const double *w, double *u, double *wdot)
+{
+    if (!c || !u) return set_error(ZM_ERR_INVALID, "zm_velocity: null context or u");
+    if ((z == nullptr) != (w == nullptr))
+        return set_error(ZM_ERR_INVALID, "zm_velocity: give both z and w, or neither");
+    const size_t N = c->geom.N;
+    const double *y = c->y0;
+    int rc = ZM_OK;
+    if (z) {
+        rc = copy_in(c, c->ya, z, 3 * N);
+        if (!rc) rc = copy_in(c, c->ya + 3 * N, w, 2 * N);
+        y = c->ya;
+    }
+    if (!rc) rc = derivative(c, y);
+    bool host = false;
+    if (!rc && wdot) {
+        if (is_device_ptr(wdot)) {
+            rc = launch_vorticity(c, y, wdot, nullptr, nullptr, 0, 0, 0, 0);
+        } else {
+            rc = launch_vorticity(c, y, c->yb, nullptr, nullptr, 0, 0, 0, 0);
+            if (!rc) rc = copy_out(c, wdot, c->yb, 2 * N, &host);
+        }
+    }
+    if (!rc) rc = copy_out(c, u, c->u, 3 * N, &host);
+    if (!rc && host) rc = read_status(c);
+    return rc;
+}
+
+int zm_step(zm_ctx *c, double dt, int nsteps)
+{
+    if (!c) return set_error(ZM_ERR_INVALID, "zm_step: null context");
+    if (!std::isfinite(dt) || nsteps < 0)
+        return set_error(ZM_ERR_INVALID, "zm_step: dt must be finite and nsteps >= 0");
+    // SSP-RK3 (Shu-Osher): stage s writes ca[s] * y0 + cb[s] * (y_s + dt L(y_s))
+    static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int s = 0; s < nsteps; ++s) {
+        const double *yin[3] = {c->y0, c->ya, c->yb};
+        double *yout[3] = {c->ya, c->yb, c->y0};
+        for (int st = 0; st < 3; ++st) {
+            int rc = derivative(c, yin[st]);
+            if (!rc) rc = launch_vorticity(c, yin[st], nullptr, c->y0, yout[st], dt, ca[st], cb[st], 1);
+            if (rc) return rc;
+        }
+    }
+    return ZM_OK;
+}
+
+int zm_check_finite(zm_ctx *c)
+{
+    if (!c) return set_error(ZM_ERR_INVALID, "zm_check_finite: null context");
+    int rc = check_finite(c, c->y0, 5 * (size_t)c->geom.N, c->flag);
+    int h = 0;
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                             "finite flag read");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream), "zm_check_finite");
+    if (!rc && h) rc = set_error(ZM_ERR_NONFINITE, "zm_check_finite: state holds NaN or Inf");
+    return rc;
+}
+
+int zm_sync(zm_ctx *c)
+{
+    if (!c) return set_error(ZM_ERR_INVALID, "zm_sync: null context");
+    return read_status(c);
+}
+
+int zm_set_profiling(zm_ctx *c, int on)
+{
+    if (!c) return set_error(ZM_ERR_INVALID, "zm_set_profiling: null context");
+    if (on) zm_reset_profile(c);
+    c->profiling = on ? 1 : 0;
+    return ZM_OK;
+}
+
+int zm_reset_profile(zm_ctx *c)
+{
+    if (!c) return set_error(ZM_ERR_INVALID, "zm_reset_profile: null context");
+    prof_fold(c);
+    std::memset(&c->prof, 0, sizeof(c->prof));
+    return ZM_OK;
+}
+
+int zm_get_profile(zm_ctx *c, zm_profile *out)
+{
+    if (!c || !out) return set_error(ZM_ERR_INVALID, "zm_get_profile: null argument");
+    prof_fold(c);
+    int rc = cuda_check(cudaStreamSynchronize(c->stream), "zm_get_profile");
+    *out = c->prof;
+    return rc;
+}
+
+}  // extern "C"

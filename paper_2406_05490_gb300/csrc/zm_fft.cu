@@ -1,0 +1,219 @@
+// zm_fft.cu -- low-order velocity by FFT Riesz transforms (paper Sec. 2: the low-order Z-Model
+// approximates the Birkhoff-Rott integral with FFTs; Sec. 3.1 ZModel Order::Low; periodic only):
+//     s = R1 w1 + R2 w2,  R_l^(k) = -i k_l / |k|,  k_l = 2 pi m_l / L_l,
+//     multiplier zero at k = 0 and on the Nyquist row and column;  u = -1/2 s N,
+//     Phi = q + 1/2 |u|^2.
+// Single-GPU design (no distributed FFT): the two real fields are packed as c = w1 + i w2 and
+// one complex transform suffices, because s = Re IFFT[(m1 - i m2) FFT(c)] with m_l = -i k_l/|k|
+// (the imaginary part of that inverse is R1 w2 - R2 w1 and is dropped).  Three passes, each
+// reading and writing the n1 x n2 complex field once:
+//   pass A: rows (along alpha2) forward, transposed write          [n1][n2] -> [n2][n1]
+//   pass B: rows of the transpose (along alpha1) forward, multiply by -(k2 + i k1)/|k|,
+//           inverse along alpha1, transposed write                  [n2][n1] -> [n1][n2]
+//   pass C: rows inverse along alpha2, real part / (n1 n2), epilogue u = -s/2 N, Phi.
+// Each CTA holds `rows` complete rows in shared memory and runs radix-2 butterflies there:
+// decimation in frequency (natural order in, bit-reversed out) for the forward transforms and
+// for pass C, decimation in time (bit-reversed in, natural out) for the inverse of pass B.
+#include <algorithm>
+
+#include "zm_internal.cuh"
+
+namespace zm {
+namespace {
+
+constexpr int kFftTpb = 256;
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+__device__ __forceinline__ int bitrev(int j, int logL) { return (int)(__brev((unsigned)j) >> (32 - logL)); }
+
+// tw[k] = exp(-2 pi i k / L), k < L/2.  sgn = +1 uses conj (inverse transform).
+__device__ __forceinline__ double2 twiddle(const double2 *__restrict__ tw, int k, int sgn)
+{
+    double2 w = tw[k];
+    if (sgn > 0) w.y = -w.y;
+    return w;
+}
+
+// Decimation in frequency, in place on `rows` rows of length L in shared memory.
+__device__ void fft_dif(double2 *x, int rows, int L, const double2 *__restrict__ tw, int sgn)
+{
+    const int half = L >> 1;
+    for (int h = half; h >= 1; h >>= 1) {
+        const int tstride = half / h;  // twiddle index step for this stage
+        for (int b = threadIdx.x; b < rows * half; b += blockDim.x) {
+            const int row = b / half, idx = b - row * half;
+            const int pos = idx & (h - 1), a = ((idx - pos) << 1) + pos;
+            double2 *xr = x + (size_t)row * L;
+            const double2 u = xr[a], v = xr[a + h];
+            xr[a] = make_double2(u.x + v.x, u.y + v.y);
+            xr[a + h] = cmul(make_double2(u.x - v.x, u.y - v.y), twiddle(tw, pos * tstride, sgn));
+        }
+        __syncthreads();
+    }
+}
+
+// Decimation in time, in place (bit-reversed input, natural output).
+__device__ void fft_dit(double2 *x, int rows, int L, const double2 *__restrict__ tw, int sgn)
+{
+    const int half = L >> 1;
+    for (int h = 1; h <= half; h <<= 1) {
+        const int tstride = half / h;
+        for (int b = threadIdx.x; b < rows * half; b += blockDim.x) {
+            const int row = b / half, idx = b - row * half;
+            const int pos = idx & (h - 1), a = ((idx - pos) << 1) + pos;
+            double2 *xr = x + (size_t)row * L;
+            const double2 u = xr[a], v = cmul(xr[a + h], twiddle(tw, pos * tstride, sgn));
+            xr[a] = make_double2(u.x + v.x, u.y + v.y);
+            xr[a + h] = make_double2(u.x - v.x, u.y - v.y);
+        }
+        __syncthreads();
+    }
+}
+
+// pass A: rows i of length n2 from w1 + i w2; forward; write out[j][i] (transposed).
+__global__ void __launch_bounds__(kFftTpb)
+    pass_a(int n1, int n2, int log2n2, int rows, const double *__restrict__ w,
+           const double2 *__restrict__ tw2, double2 *__restrict__ out)
+{
+    extern __shared__ double2 sx[];
+    const int i0 = blockIdx.x * rows;
+    const size_t N = (size_t)n1 * n2;
+    for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
+        const int r = e / n2, j = e - r * n2;
+        const size_t p = (size_t)(i0 + r) * n2 + j;
+        sx[e] = make_double2(w[p], w[N + p]);
+    }
+    __syncthreads();
+    fft_dif(sx, rows, n2, tw2, -1);
+    for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
+        const int j = e / rows, r = e - j * rows;
+        out[(size_t)j * n1 + i0 + r] = sx[(size_t)r * n2 + bitrev(j, log2n2)];
+    }
+}
+
+// pass B: rows j (length n1) of the transpose; forward; multiply; inverse; write out[i][j].
+__global__ void __launch_bounds__(kFftTpb)
+    pass_b(int n1, int n2, int log2n1, int rows, double L1, double L2,
+           const double2 *__restrict__ in, const double2 *__restrict__ tw1, double2 *__restrict__ out)
+{
+    extern __shared__ double2 sx[];
+    const int j0 = blockIdx.x * rows;
+    for (int e = threadIdx.x; e < rows * n1; e += blockDim.x) sx[e] = in[(size_t)j0 * n1 + e];
+    __syncthreads();
+    fft_dif(sx, rows, n1, tw1, -1);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int e = threadIdx.x; e < rows * n1; e += blockDim.x) {
+        const int r = e / n1, pos = e - r * n1;
+        const int i = bitrev(pos, log2n1), j = j0 + r;  // frequency indices
+        const int m1 = (i < n1 / 2) ? i : i - n1;
+        const int m2 = (j < n2 / 2) ? j : j - n2;
+        double2 v = make_double2(0.0, 0.0);
+        if (!(m1 == 0 && m2 == 0) && 2 * i != n1 && 2 * j != n2) {
+            const double k1 = two_pi * m1 / L1, k2 = two_pi * m2 / L2;
+            const double ik = 1.0 / sqrt(k1 * k1 + k2 * k2);
+            // multiplier -(k2 + i k1) / |k|
+            v = cmul(sx[e], make_double2(-k2 * ik, -k1 * ik));
+        }
+        sx[e] = v;
+    }
+    __syncthreads();
+    fft_dit(sx, rows, n1, tw1, +1);
+    for (int e = threadIdx.x; e < rows * n1; e += blockDim.x) {
+        const int i = e / rows, r = e - i * rows;
+        out[(size_t)i * n2 + j0 + r] = sx[(size_t)r * n1 + i];
+    }
+}
+
+// pass C: rows i (length n2); inverse; s = Re / (n1 n2); u = -s/2 N; Phi = q + |u|^2 / 2.
+__global__ void __launch_bounds__(kFftTpb)
+    pass_c(int n1, int n2, int log2n2, int rows, const double2 *__restrict__ in,
+           const double2 *__restrict__ tw2, const double *__restrict__ nrm,
+           const double *__restrict__ q, double *__restrict__ u, double *__restrict__ phi)
+{
+    extern __shared__ double2 sx[];
+    const int i0 = blockIdx.x * rows;
+    const size_t N = (size_t)n1 * n2;
+    for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) sx[e] = in[(size_t)i0 * n2 + e];
+    __syncthreads();
+    fft_dif(sx, rows, n2, tw2, +1);
+    const double inv = 1.0 / ((double)n1 * (double)n2);
+    for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
+        const int r = e / n2, j = e - r * n2;
+        const size_t p = (size_t)(i0 + r) * n2 + j;
+        const double s = sx[(size_t)r * n2 + bitrev(j, log2n2)].x * inv;
+        const double ux = -0.5 * s * nrm[p], uy = -0.5 * s * nrm[N + p], uz = -0.5 * s * nrm[2 * N + p];
+        u[p] = ux;
+        u[N + p] = uy;
+        u[2 * N + p] = uz;
+        phi[p] = q[p] + 0.5 * (ux * ux + uy * uy + uz * uz);
+    }
+}
+
+__global__ void twiddle_kernel(int L, double2 *tw)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L / 2) return;
+    double s, c;
+    sincospi(-2.0 * (double)k / (double)L, &s, &c);
+    tw[k] = make_double2(c, s);
+}
+
+int ilog2(int n)
+{
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+int rows_for(int L) { return std::max(1, std::min(8, 4096 / L)); }
+
+}  // namespace
+
+int fft_setup(zm_ctx *c)
+{
+    const Geom &g = c->geom;
+    const size_t N = g.N;
+    if (cudaMalloc(&c->fa, N * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&c->fb, N * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&c->tw1, (g.n1 / 2) * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&c->tw2, (g.n2 / 2) * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ZM_ERR_NOMEM, "fft_setup: device allocation failed");
+    }
+    twiddle_kernel<<<(g.n1 / 2 + 255) / 256, 256>>>(g.n1, c->tw1);
+    twiddle_kernel<<<(g.n2 / 2 + 255) / 256, 256>>>(g.n2, c->tw2);
+    const int smax = 8 * 4096 * (int)sizeof(double2) / 8;  // rows * L * 16 <= 64 KiB
+    int rc = cuda_check(cudaFuncSetAttribute(pass_a, cudaFuncAttributeMaxDynamicSharedMemorySize, smax),
+                        "fft smem attribute");
+    if (!rc) rc = cuda_check(cudaFuncSetAttribute(pass_b, cudaFuncAttributeMaxDynamicSharedMemorySize, smax),
+                             "fft smem attribute");
+    if (!rc) rc = cuda_check(cudaFuncSetAttribute(pass_c, cudaFuncAttributeMaxDynamicSharedMemorySize, smax),
+                             "fft smem attribute");
+    if (!rc) rc = cuda_check(cudaGetLastError(), "twiddle kernel");
+    return rc;
+}
+
+int launch_riesz(zm_ctx *c, const double *y)
+{
+    const Geom &g = c->geom;
+    const int l1 = ilog2(g.n1), l2 = ilog2(g.n2);
+    const int ra = rows_for(g.n2), rb = rows_for(g.n1);
+    const double *w = y + 3 * (size_t)g.N;
+    cudaEvent_t ev = nullptr;
+    prof_begin(c, ZM_K_FFT, &ev);
+    pass_a<<<g.n1 / ra, kFftTpb, ra * g.n2 * sizeof(double2), c->stream>>>(g.n1, g.n2, l2, ra, w,
+                                                                            c->tw2, c->fa);
+    pass_b<<<g.n2 / rb, kFftTpb, rb * g.n1 * sizeof(double2), c->stream>>>(
+        g.n1, g.n2, l1, rb, g.L1, g.L2, c->fa, c->tw1, c->fb);
+    pass_c<<<g.n1 / ra, kFftTpb, ra * g.n2 * sizeof(double2), c->stream>>>(
+        g.n1, g.n2, l2, ra, c->fb, c->tw2, c->nrm, c->q, c->u, c->phi);
+    prof_end(c, ZM_K_FFT, ev);
+    c->prof.launches[ZM_K_FFT] += 2;  // three kernels per Riesz evaluation
+    return cuda_check(cudaGetLastError(), "Riesz FFT launch");
+}
+
+}  // namespace zm

@@ -1,0 +1,200 @@
+// zm_internal.cuh -- internal declarations shared by the translation units of libzm.so.
+// Not part of the public ABI (include/zm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "zm.h"
+
+namespace zm {
+
+// Mesh constants handed to every stencil kernel by value.
+struct Geom {
+    int n1, n2, N;
+    double dx1, dx2, L1, L2;
+    int periodic;
+};
+
+// Source records of the Birkhoff-Rott sum are stored tile-major: a tile is a tp1 x tp2 patch of
+// the mesh (compact in space for a smooth interface), ts = tp1 * tp2 slots, padded with
+// zero-strength sources where the patch runs past the mesh edge.
+struct Tiling {
+    int tp1, tp2, ts;
+    int nt1, nt2, ntiles;
+};
+
+// FP64 record: rows 0-2 absolute position, rows 3-5 scaled sheet strength -> [tile][6][ts] double
+// FP32C record: rows 0-2 position hi, 3-5 position lo, 6-8 scaled strength -> [tile][9][ts] float
+constexpr int kRec64 = 6;
+constexpr int kRec32 = 9;
+
+// Launch geometry of the all-pairs kernel.
+struct BrPlan {
+    int tpb;        // threads per CTA
+    int r;          // targets per thread (register blocking)
+    int nsplit;     // source splits (grid.y); partial sums reduced by a second kernel
+    int tiles_per_split;
+    int ntb;        // target blocks (grid.x)
+};
+
+// Device-side status word bits.
+constexpr int kErrTimeout = 1;
+
+}  // namespace zm
+
+struct zm_ctx {
+    zm_mesh mesh;
+    zm::Geom geom;
+    double atwood, g, mu, delta;
+    int order;  // ZM_ORDER_*
+    int fp32c;  // reduced-precision Birkhoff-Rott pair terms
+    int device;
+    cudaStream_t stream;
+
+    // state and stage buffers: 5N doubles each, (z1, z2, z3, w1, w2) component-major
+    double *y0, *ya, *yb;
+    double *u;    // 3N velocity of the last derivative evaluation
+    double *phi;  // N
+    double *q;    // N: g z3 + 1/8 w^T h^-1 w (the part of Phi that does not need u)
+    double *nrm;  // 3N unit normals (low order)
+
+    // Birkhoff-Rott source records and split partial sums
+    zm::Tiling tiling;
+    zm::BrPlan plan;
+    void *src;
+    size_t src_bytes;
+    double *part;  // [nsplit][3][N]
+
+    // low order: FFT workspace (complex doubles) and twiddles
+    double2 *fa, *fb, *tw1, *tw2;
+
+    int *err;   // device status word (zm::kErr*)
+    int *flag;  // device scratch flag (finite check)
+
+    // profiling
+    int profiling;
+    zm_profile prof;
+    struct Ev {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Ev> ev_live;
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+namespace zm {
+
+// ---- error reporting (zm_api.cu) ------------------------------------------------------------
+int set_error(int code, const std::string &msg);
+int cuda_check(cudaError_t e, const char *what);
+
+// ---- profiling helpers (zm_api.cu) -----------------------------------------------------------
+void prof_begin(zm_ctx *c, int cls, cudaEvent_t *a);
+void prof_end(zm_ctx *c, int cls, cudaEvent_t a);
+
+// ---- stencil kernels (zm_stencil.cu) -----------------------------------------------------------
+// Geometry pass over state y (5N): writes source records (high order), q, and normals (low).
+int launch_geometry(zm_ctx *c, const double *y);
+// Vorticity pass.  mode 0: wdot_out = dw/dt (2N) from phi and y.  mode 1: RK3 stage combine
+// yout = ca * y0 + cb * (y + dt * L(y)), L = (u, dw/dt).
+int launch_vorticity(zm_ctx *c, const double *y, double *wdot_out, const double *y0, double *yout,
+                     double dt, double ca, double cb, int mode);
+// Reduce split partials into u and phi.
+int launch_reduce(zm_ctx *c);
+// Set *dev_flag (device int) to 1 if any of y[0..n) is NaN/Inf.
+int check_finite(zm_ctx *c, const double *y, size_t n, int *dev_flag);
+
+// ---- Birkhoff-Rott kernels (zm_br.cu) ----------------------------------------------------------
+BrPlan plan_br(const Geom &g, const Tiling &t, int fp32c, int sm_count);
+Tiling make_tiling(const Geom &g);
+int launch_br(zm_ctx *c, const double *y);
+
+// ---- low order (zm_fft.cu) ---------------------------------------------------------------------
+int fft_setup(zm_ctx *c);
+int launch_riesz(zm_ctx *c, const double *y);
+
+// ---- one full derivative evaluation (zm_api.cu) --------------------------------------------------
+int derivative(zm_ctx *c, const double *y);
+
+}  // namespace zm
+
+// ---- device helpers ------------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace zm {
+namespace dev {
+
+// Bounded waits: every spin on an mbarrier gives up after this many polls and reports
+// kErrTimeout through the status word instead of hanging the GPU.
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Arm the barrier for `bytes` of asynchronous transactions and start one 1D bulk TMA copy
+// global -> shared that completes them.  Both addresses 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void tma_load_1d(void *smem_dst, const void *gmem_src, uint32_t bytes,
+                                            uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(smem_dst)),
+        "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Returns false if the phase did not complete within kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+}  // namespace dev
+}  // namespace zm
+#endif

@@ -1,0 +1,250 @@
+// zm_stencil.cu -- surface-mesh stencil kernels (FP64):
+//   geometry pass: two-deep ghosts, tangents a1 = D1 z, a2 = D2 z, metric, unit normal, the
+//     sheet strength gamma = w1 a2 - w2 a1 written as Birkhoff-Rott source records, and
+//     q = g z3 + 1/8 w^T h^-1 w (paper Sec. 2 ZModel "surface normals"; Sec. 3.1 SurfaceMesh
+//     two-node-deep stencils and BoundaryCondition ghost rules);
+//   reduction of split Birkhoff-Rott partials into u and Phi = q + 1/2 |u|^2;
+//   vorticity pass: dw_l/dt = -2 A D_l Phi + mu Lap w_l, fused with the SSP-RK3 stage combine
+//     (Sec. 3.1 TimeIntegrator, three derivative evaluations per step).
+// One thread per mesh node; neighbours come through L1/L2, so each kernel streams its fields
+// once from HBM.
+#include "zm_internal.cuh"
+
+namespace zm {
+namespace {
+
+constexpr int kTpb = 256;
+
+// The five values f[c-2 .. c+2] along one axis of node (i, j), with two-deep ghosts:
+// periodic: wrap and add +-seam (the period jump of the field across the seam: L1 for z1 along
+// alpha1, L2 for z2 along alpha2, zero otherwise); free edges: odd reflection about the edge
+// node, i.e. linear extrapolation f(edge - m) = 2 f(edge) - f(edge + m).
+__device__ __forceinline__ void line5(const double *__restrict__ f, int i, int j, int axis,
+                                      const Geom &g, double seam, double v[5])
+{
+    const int n = axis ? g.n2 : g.n1;
+    const int c0 = axis ? j : i;
+    const size_t stride = axis ? 1 : (size_t)g.n2;
+    const double *base = axis ? f + (size_t)i * g.n2 : f + j;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int c = c0 + k - 2;
+        if (c >= 0 && c < n) {
+            v[k] = base[c * stride];
+        } else if (g.periodic) {
+            v[k] = (c < 0) ? base[(c + n) * stride] - seam : base[(c - n) * stride] + seam;
+        } else {
+            v[k] = (c < 0) ? 2.0 * base[0] - base[(-c) * stride]
+                           : 2.0 * base[(n - 1) * stride] - base[(2 * (n - 1) - c) * stride];
+        }
+    }
+}
+
+// 4th-order first and second differences of five samples spaced dx apart.
+__device__ __forceinline__ double diff1(const double v[5], double inv12dx)
+{
+    return ((v[0] - v[4]) + 8.0 * (v[3] - v[1])) * inv12dx;
+}
+__device__ __forceinline__ double diff2(const double v[5], double inv12dx2)
+{
+    return (16.0 * (v[1] + v[3]) - (v[0] + v[4]) - 30.0 * v[2]) * inv12dx2;
+}
+
+template <bool kFp32c, bool kLow>
+__global__ void __launch_bounds__(kTpb)
+    geometry_kernel(Geom g, Tiling t, const double *__restrict__ y, double pref, double grav,
+                    void *__restrict__ src, double *__restrict__ q, double *__restrict__ nrm)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.N) return;
+    const int i = p / g.n2, j = p - (p / g.n2) * g.n2;
+    const double *z = y, *w = y + 3 * (size_t)g.N;
+    const double i12a = 1.0 / (12.0 * g.dx1), i12b = 1.0 / (12.0 * g.dx2);
+
+    double a1[3], a2[3], v[5];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        line5(z + (size_t)c * g.N, i, j, 0, g, c == 0 ? g.L1 : 0.0, v);
+        a1[c] = diff1(v, i12a);
+        line5(z + (size_t)c * g.N, i, j, 1, g, c == 1 ? g.L2 : 0.0, v);
+        a2[c] = diff1(v, i12b);
+    }
+    const double h11 = a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2];
+    const double h12 = a1[0] * a2[0] + a1[1] * a2[1] + a1[2] * a2[2];
+    const double h22 = a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2];
+    const double det = h11 * h22 - h12 * h12;
+    const double w1 = w[p], w2 = w[(size_t)g.N + p];
+    const double z3 = z[2 * (size_t)g.N + p];
+    q[p] = grav * z3 + 0.125 * (h22 * w1 * w1 - 2.0 * h12 * w1 * w2 + h11 * w2 * w2) / det;
+
+    if (kLow) {
+        const double nx = a1[1] * a2[2] - a1[2] * a2[1];
+        const double ny = a1[2] * a2[0] - a1[0] * a2[2];
+        const double nz = a1[0] * a2[1] - a1[1] * a2[0];
+        const double il = 1.0 / sqrt(nx * nx + ny * ny + nz * nz);
+        nrm[p] = nx * il;
+        nrm[(size_t)g.N + p] = ny * il;
+        nrm[2 * (size_t)g.N + p] = nz * il;
+        return;
+    }
+    // scaled sheet strength gamma' = (dx1 dx2 / 4 pi) (w1 a2 - w2 a1)
+    double gm[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gm[c] = pref * (w1 * a2[c] - w2 * a1[c]);
+
+    const int ti = i / t.tp1, tj = j / t.tp2;
+    const size_t tile = (size_t)ti * t.nt2 + tj;
+    const int slot = (i - ti * t.tp1) * t.tp2 + (j - tj * t.tp2);
+    if (kFp32c) {
+        float *r = static_cast<float *>(src) + tile * kRec32 * t.ts + slot;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double zc = z[(size_t)c * g.N + p];
+            const float hi = __double2float_rn(zc);
+            r[(size_t)c * t.ts] = hi;
+            r[(size_t)(3 + c) * t.ts] = __double2float_rn(zc - (double)hi);
+            r[(size_t)(6 + c) * t.ts] = __double2float_rn(gm[c]);
+        }
+    } else {
+        double *r = static_cast<double *>(src) + tile * kRec64 * t.ts + slot;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            r[(size_t)c * t.ts] = z[(size_t)c * g.N + p];
+            r[(size_t)(3 + c) * t.ts] = gm[c];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTpb)
+    reduce_kernel(int N, int nsplit, const double *__restrict__ part, const double *__restrict__ q,
+                  double *__restrict__ u, double *__restrict__ phi)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < nsplit; ++k) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s[c] += part[((size_t)k * 3 + c) * N + p];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[(size_t)c * N + p] = s[c];
+    phi[p] = q[p] + 0.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+}
+
+// mode 0: write dw/dt.  mode 1: yout = ca * y0 + cb * (y + dt * (u, dw/dt)).
+template <bool kVisc, int kMode>
+__global__ void __launch_bounds__(kTpb)
+    vorticity_kernel(Geom g, const double *__restrict__ phi, const double *__restrict__ y,
+                     const double *__restrict__ u, double atwood, double mu, double dt, double ca,
+                     double cb, const double *y0, double *yout, double *__restrict__ wdot)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.N) return;
+    const int i = p / g.n2, j = p - (p / g.n2) * g.n2;
+    const size_t N = g.N;
+    double v[5];
+    line5(phi, i, j, 0, g, 0.0, v);
+    double f1 = -2.0 * atwood * diff1(v, 1.0 / (12.0 * g.dx1));
+    line5(phi, i, j, 1, g, 0.0, v);
+    double f2 = -2.0 * atwood * diff1(v, 1.0 / (12.0 * g.dx2));
+    if (kVisc) {
+        const double ia = 1.0 / (12.0 * g.dx1 * g.dx1), ib = 1.0 / (12.0 * g.dx2 * g.dx2);
+        const double *w = y + 3 * N;
+        line5(w, i, j, 0, g, 0.0, v);
+        double l1 = diff2(v, ia);
+        line5(w, i, j, 1, g, 0.0, v);
+        l1 += diff2(v, ib);
+        line5(w + N, i, j, 0, g, 0.0, v);
+        double l2 = diff2(v, ia);
+        line5(w + N, i, j, 1, g, 0.0, v);
+        l2 += diff2(v, ib);
+        f1 += mu * l1;
+        f2 += mu * l2;
+    }
+    if (kMode == 0) {
+        wdot[p] = f1;
+        wdot[N + p] = f2;
+        return;
+    }
+    const double d[5] = {u[p], u[N + p], u[2 * N + p], f1, f2};
+    double out[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[c] = ca * y0[c * N + p] + cb * (y[c * N + p] + dt * d[c]);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) yout[c * N + p] = out[c];
+}
+
+__global__ void finite_kernel(size_t n, const double *__restrict__ y, int *bad)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        if (!isfinite(y[k])) {
+            atomicOr(bad, 1);
+            return;
+        }
+}
+
+}  // namespace
+
+int check_finite(zm_ctx *c, const double *y, size_t n, int *dev_flag)
+{
+    int rc = cuda_check(cudaMemsetAsync(dev_flag, 0, sizeof(int), c->stream), "finite flag clear");
+    if (rc) return rc;
+    finite_kernel<<<4 * 152, kTpb, 0, c->stream>>>(n, y, dev_flag);
+    return cuda_check(cudaGetLastError(), "finite check launch");
+}
+
+int launch_geometry(zm_ctx *c, const double *y)
+{
+    const Geom &g = c->geom;
+    const double pref = g.dx1 * g.dx2 / (4.0 * 3.14159265358979323846);
+    dim3 grid((g.N + kTpb - 1) / kTpb);
+    cudaEvent_t ev = nullptr;
+    prof_begin(c, ZM_K_GEOMETRY, &ev);
+    const bool low = (c->order == ZM_ORDER_LOW);
+    if (low)
+        geometry_kernel<false, true><<<grid, kTpb, 0, c->stream>>>(g, c->tiling, y, pref, c->g,
+                                                                  nullptr, c->q, c->nrm);
+    else if (c->fp32c)
+        geometry_kernel<true, false><<<grid, kTpb, 0, c->stream>>>(g, c->tiling, y, pref, c->g,
+                                                                  c->src, c->q, nullptr);
+    else
+        geometry_kernel<false, false><<<grid, kTpb, 0, c->stream>>>(g, c->tiling, y, pref, c->g,
+                                                                   c->src, c->q, nullptr);
+    prof_end(c, ZM_K_GEOMETRY, ev);
+    return cuda_check(cudaGetLastError(), "geometry kernel launch");
+}
+
+int launch_reduce(zm_ctx *c)
+{
+    const Geom &g = c->geom;
+    dim3 grid((g.N + kTpb - 1) / kTpb);
+    cudaEvent_t ev = nullptr;
+    prof_begin(c, ZM_K_REDUCE, &ev);
+    reduce_kernel<<<grid, kTpb, 0, c->stream>>>(g.N, c->plan.nsplit, c->part, c->q, c->u, c->phi);
+    prof_end(c, ZM_K_REDUCE, ev);
+    return cuda_check(cudaGetLastError(), "reduce kernel launch");
+}
+
+int launch_vorticity(zm_ctx *c, const double *y, double *wdot_out, const double *y0, double *yout,
+                     double dt, double ca, double cb, int mode)
+{
+    const Geom &g = c->geom;
+    dim3 grid((g.N + kTpb - 1) / kTpb);
+    cudaEvent_t ev = nullptr;
+    prof_begin(c, ZM_K_VORT, &ev);
+    const bool visc = (c->mu != 0.0);
+#define ZM_VORT(V, M)                                                                          \
+    vorticity_kernel<V, M><<<grid, kTpb, 0, c->stream>>>(g, c->phi, y, c->u, c->atwood, c->mu, \
+                                                         dt, ca, cb, y0, yout, wdot_out)
+    if (mode == 0) {
+        if (visc) ZM_VORT(true, 0); else ZM_VORT(false, 0);
+    } else {
+        if (visc) ZM_VORT(true, 1); else ZM_VORT(false, 1);
+    }
+#undef ZM_VORT
+    prof_end(c, ZM_K_VORT, ev);
+    return cuda_check(cudaGetLastError(), "vorticity kernel launch");
+}
+
+}  // namespace zm

@@ -1,0 +1,242 @@
+"""Thin ctypes binding of libzm.so (include/zm.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; this module converts
+arguments (numpy arrays, torch tensors on CPU or GPU, or raw integer addresses) to pointers and
+raises ZMError on a non-zero status.  If the shared library has not been built the first call
+raises immediately: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ZM_OK = 0
+ZM_ERR_INVALID = -1
+ZM_ERR_NOMEM = -2
+ZM_ERR_CUDA = -3
+ZM_ERR_TIMEOUT = -4
+ZM_ERR_UNSUPPORTED = -5
+ZM_ERR_NONFINITE = -6
+ZM_ERR_BUSY = -7
+
+ZM_ORDER_LOW = 0
+ZM_ORDER_MEDIUM = 1
+ZM_ORDER_HIGH = 2
+ZM_PREC_FP64 = 0x000
+ZM_PREC_FP32C = 0x100
+
+ZM_K_GEOMETRY, ZM_K_BR, ZM_K_REDUCE, ZM_K_VORT, ZM_K_FFT, ZM_K_COUNT = range(6)
+KERNEL_NAMES = ["geometry", "br", "reduce", "vorticity", "fft"]
+
+
+class ZMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class zm_mesh(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int32), ("n2", ctypes.c_int32), ("L1", ctypes.c_double),
+                ("L2", ctypes.c_double), ("periodic", ctypes.c_int32)]
+
+
+class zm_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * ZM_K_COUNT), ("launches", ctypes.c_int64 * ZM_K_COUNT),
+                ("pairs", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+VP = ctypes.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libzm.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise ZMError(ZM_ERR_CUDA, f"libzm.so not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        I, D = ctypes.c_int, ctypes.c_double
+        sig = {
+            "zm_create": (I, [ctypes.POINTER(zm_mesh), D, D, D, D, I, ctypes.POINTER(VP)]),
+            "zm_set_stream": (I, [VP, VP]),
+            "zm_set_state": (I, [VP, VP, VP]),
+            "zm_get_state": (I, [VP, VP, VP]),
+            "zm_velocity": (I, [VP, VP, VP, VP, VP]),
+            "zm_step": (I, [VP, D, I]),
+            "zm_sync": (I, [VP]),
+            "zm_destroy": (None, [VP]),
+            "zm_error_string": (ctypes.c_char_p, [I]),
+            "zm_last_error": (ctypes.c_char_p, []),
+            "zm_set_profiling": (I, [VP, I]),
+            "zm_get_profile": (I, [VP, ctypes.POINTER(zm_profile)]),
+            "zm_reset_profile": (I, [VP]),
+            "zm_check_finite": (I, [VP]),
+            "zm_measure_peak": (I, [I, ctypes.POINTER(D)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(code):
+    if code != ZM_OK:
+        lib = load()
+        raise ZMError(code, f"{lib.zm_error_string(code).decode()}: {lib.zm_last_error().decode()}")
+
+
+def ptr(x):
+    """Address of a float64 contiguous buffer: numpy array, torch tensor, int address or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ZMError(ZM_ERR_INVALID, "numpy buffers must be C-contiguous float64")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ZMError(ZM_ERR_INVALID, "torch buffers must be contiguous float64")
+        return x.data_ptr()
+    raise ZMError(ZM_ERR_INVALID, f"unsupported buffer type {type(x)}")
+
+
+# ---- the C ABI, one function per entry point ------------------------------------------------
+
+def zm_create(n1, n2=None, L1=1.0, L2=1.0, periodic=True, atwood=0.5, g=1.0, mu=0.0, delta=None,
+              order=ZM_ORDER_HIGH):
+    lib = load()
+    n2 = n1 if n2 is None else n2
+    if delta is None:
+        delta = 0.1 * L1 / n1
+    m = zm_mesh(int(n1), int(n2), float(L1), float(L2), int(bool(periodic)))
+    h = VP()
+    _check(lib.zm_create(ctypes.byref(m), float(atwood), float(g), float(mu), float(delta), int(order),
+                         ctypes.byref(h)))
+    return h
+
+
+def zm_set_stream(h, stream):
+    _check(load().zm_set_stream(h, stream))
+
+
+def zm_set_state(h, z, w):
+    _check(load().zm_set_state(h, ptr(z), ptr(w)))
+
+
+def zm_get_state(h, z, w):
+    _check(load().zm_get_state(h, ptr(z), ptr(w)))
+
+
+def zm_velocity(h, z, w, u, wdot=None):
+    _check(load().zm_velocity(h, ptr(z), ptr(w), ptr(u), ptr(wdot)))
+
+
+def zm_step(h, dt, nsteps):
+    _check(load().zm_step(h, float(dt), int(nsteps)))
+
+
+def zm_sync(h):
+    _check(load().zm_sync(h))
+
+
+def zm_destroy(h):
+    if h:
+        load().zm_destroy(h)
+
+
+def zm_set_profiling(h, on):
+    _check(load().zm_set_profiling(h, int(bool(on))))
+
+
+def zm_get_profile(h):
+    p = zm_profile()
+    _check(load().zm_get_profile(h, ctypes.byref(p)))
+    return {"ms": {KERNEL_NAMES[k]: p.ms[k] for k in range(ZM_K_COUNT)},
+            "launches": {KERNEL_NAMES[k]: int(p.launches[k]) for k in range(ZM_K_COUNT)},
+            "pairs": int(p.pairs)}
+
+
+def zm_reset_profile(h):
+    _check(load().zm_reset_profile(h))
+
+
+def zm_check_finite(h):
+    return load().zm_check_finite(h)
+
+
+PEAK_FP32, PEAK_FP64, PEAK_RSQRT = 0, 1, 2
+
+
+def zm_measure_peak(kind):
+    v = ctypes.c_double()
+    _check(load().zm_measure_peak(int(kind), ctypes.byref(v)))
+    return v.value
+
+
+# ---- a small convenience wrapper -------------------------------------------------------------
+
+class ZModel:
+    """One interface on the current GPU; owns a zm_ctx.  Arrays are (3, N) / (2, N) float64."""
+
+    def __init__(self, n1, n2=None, L1=1.0, L2=1.0, periodic=True, atwood=0.5, g=1.0, mu=0.0,
+                 delta=None, order=ZM_ORDER_HIGH, fp32c=False, stream=None):
+        self.n1 = int(n1)
+        self.n2 = int(n1 if n2 is None else n2)
+        self.N = self.n1 * self.n2
+        self.order = order | (ZM_PREC_FP32C if fp32c else 0)
+        self.h = zm_create(self.n1, self.n2, L1, L2, periodic, atwood, g, mu, delta, self.order)
+        if stream is not None:
+            zm_set_stream(self.h, stream)
+
+    def close(self):
+        if self.h:
+            zm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, z, w):
+        zm_set_state(self.h, z, w)
+
+    def get_state(self):
+        z = np.empty((3, self.N))
+        w = np.empty((2, self.N))
+        zm_get_state(self.h, z, w)
+        return z, w
+
+    def velocity(self, z=None, w=None, want_wdot=True):
+        u = np.empty((3, self.N))
+        wd = np.empty((2, self.N)) if want_wdot else None
+        zs = None if z is None else np.ascontiguousarray(z, dtype=np.float64)
+        ws = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        zm_velocity(self.h, zs, ws, u, wd)
+        return (u, wd) if want_wdot else u
+
+    def step(self, dt, nsteps=1):
+        zm_step(self.h, dt, nsteps)
+
+    def sync(self):
+        zm_sync(self.h)

@@ -1,0 +1,48 @@
+"""The C-ABI library loads on a CPU-only host and exports every entry point that include/*.h
+declares (no compute call is made here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(zm\w*)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("zm_create", "zm_velocity", "zm_step", "zm_destroy", "zm_set_state", "zm_get_state",
+                 "zm_set_stream", "zm_sync", "zm_error_string"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2406_05490_gb300 import build
+    lib_path = build.build()
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    # status strings are pure host code
+    lib.zm_error_string.restype = ctypes.c_char_p
+    assert lib.zm_error_string(0) == b"ok"
+    assert lib.zm_error_string(-5) == b"unsupported configuration"
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2406_05490_gb300 import zm
+    monkeypatch.setattr(zm, "_lib", None)
+    monkeypatch.setattr(zm, "lib_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(zm.ZMError):
+        zm.load()

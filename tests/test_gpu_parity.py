@@ -1,0 +1,226 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on seeded inputs.
+
+Tolerances (relative L2 per field, ||x_gpu - x_ref|| / ||x_ref|| over all nodes and components):
+  FP64 path: 1e-12 for u, dw/dt and the stepped state.
+  FP32C path (FP32 Birkhoff-Rott pair terms): 1e-6 for u; dw/dt and the stepped state are
+  reported per field and bounded by the same 1e-6 (they inherit u's error through Phi).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_05490_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-6
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def zm():
+    import torch
+    from paper_2406_05490_gb300 import zm as _zm
+    assert torch.cuda.is_available()
+    _zm.load()
+    return _zm
+
+
+SHAPES = [(16, 16, False), (32, 32, False), (48, 40, True), (37, 53, False), (64, 64, True),
+          (5, 7, False), (96, 80, True)]
+
+
+@pytest.mark.parametrize("n1,n2,periodic", SHAPES)
+@pytest.mark.parametrize("fp32c", [False, True])
+def test_velocity_parity(zm, n1, n2, periodic, fp32c):
+    z, w = inputs.random_state(n1, n2, seed=n1 * 7 + n2)
+    A, g, mu = 0.4, 1.3, (0.01 if periodic else 0.0)
+    delta = 0.1 / max(n1, n2)
+    m = oracle.Mesh(n1, n2, periodic=periodic)
+    u_ref, wd_ref = oracle.derivative(m, z, w, A, g, mu, delta)
+    model = zm.ZModel(n1, n2, periodic=periodic, atwood=A, g=g, mu=mu, delta=delta, fp32c=fp32c)
+    u, wd = model.velocity(z, w)
+    model.close()
+    tol = TOL32 if fp32c else TOL64
+    eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+    print(f"n={n1}x{n2} periodic={periodic} fp32c={fp32c}: rel L2 u={eu:.3e} wdot={ew:.3e}")
+    assert eu <= tol and ew <= tol
+
+
+def test_flat_rest_exact(zm):
+    n = 32
+    a, b = inputs.mesh_coords(n)
+    z = np.stack([a, b, 0 * a])
+    w = np.zeros((2, n * n))
+    for fp32c in (False, True):
+        model = zm.ZModel(n, periodic=False, fp32c=fp32c)
+        u, wd = model.velocity(z, w)
+        model.close()
+        assert np.all(u == 0.0) and np.all(wd == 0.0)
+
+
+@pytest.mark.parametrize("fp32c", [False, True])
+def test_single_mode_steps_config1(zm, fp32c):
+    """32 x 32 single-mode interface, free edges, A = 0.5, g = 1, delta = 0.1 dx, dt = 1e-3,
+    10 SSP-RK3 steps: final state against the oracle."""
+    n = 32
+    z0, w0 = inputs.single_mode(n)
+    m = oracle.Mesh(n, periodic=False)
+    zr, wr = oracle.run(m, z0, w0, 0.5, 1.0, 0.0, 0.1 / n, 1e-3, 10)
+    model = zm.ZModel(n, periodic=False, atwood=0.5, g=1.0, delta=0.1 / n, fp32c=fp32c)
+    model.set_state(z0, w0)
+    model.step(1e-3, 10)
+    z1, w1 = model.get_state()
+    model.close()
+    tol = TOL32 if fp32c else TOL64
+    ez, ew = rel(z1, zr), rel(w1, wr)
+    dz = rel(z1 - z0, zr - z0)
+    print(f"config1 fp32c={fp32c}: rel L2 z={ez:.3e} w={ew:.3e} (z - z0)={dz:.3e}")
+    assert ez <= tol and ew <= tol and dz <= (1e-5 if fp32c else 1e-10)
+
+
+@pytest.mark.parametrize("n1,n2", [(8, 8), (64, 32), (128, 128), (16, 256)])
+def test_low_order_parity(zm, n1, n2):
+    z, w = inputs.random_state(n1, n2, seed=n1 + n2)
+    m = oracle.Mesh(n1, n2, periodic=True)
+    u_ref, wd_ref = oracle.derivative(m, z, w, 0.7, 1.0, 0.0, 0.0, order=oracle.ORDER_LOW)
+    model = zm.ZModel(n1, n2, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW)
+    u, wd = model.velocity(z, w)
+    model.close()
+    eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+    print(f"low order {n1}x{n2}: rel L2 u={eu:.3e} wdot={ew:.3e}")
+    assert eu <= TOL64 and ew <= TOL64
+
+
+def test_low_order_steps(zm):
+    n = 64
+    z0, w0 = inputs.multi_mode(n, n_modes=8, seed=3, amp=0.02)
+    m = oracle.Mesh(n, periodic=True)
+    zr, wr = oracle.run(m, z0, w0, 0.7, 1.0, 0.0, 0.0, 1e-3, 5, order=oracle.ORDER_LOW)
+    model = zm.ZModel(n, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW)
+    model.set_state(z0, w0)
+    model.step(1e-3, 5)
+    z1, w1 = model.get_state()
+    model.close()
+    assert rel(z1, zr) <= TOL64 and rel(w1, wr) <= TOL64
+
+
+def test_multi_mode_steps_periodic(zm):
+    n = 64
+    z0, w0 = inputs.multi_mode(n, n_modes=16, seed=1)
+    m = oracle.Mesh(n, periodic=True)
+    zr, wr = oracle.run(m, z0, w0, 0.5, 1.0, 0.0, 0.1 / n, 1e-3, 3)
+    for fp32c, tol in ((False, TOL64), (True, TOL32)):
+        model = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, fp32c=fp32c)
+        model.set_state(z0, w0)
+        model.step(1e-3, 3)
+        z1, w1 = model.get_state()
+        model.close()
+        assert rel(z1, zr) <= tol and rel(w1, wr) <= tol
+
+
+@pytest.mark.parametrize("fp32c", [False, True])
+def test_full_size_sampled_256(zm, fp32c):
+    """256 x 256 periodic multi-mode interface with vorticity (one derivative evaluation in the
+    launch configuration of the 256^2 benchmark): all of u from the GPU, 1024 seeded targets
+    summed over all 65,536 sources by the oracle."""
+    n = 256
+    z, w = inputs.random_state(n, seed=11)
+    delta = 0.1 / n
+    m = oracle.Mesh(n, periodic=True)
+    a1, a2, _, _ = oracle.geometry(m, z)
+    gam = oracle.sheet_strength(w, a1, a2)
+    idx = np.random.default_rng(5).choice(n * n, 1024, replace=False)
+    u_ref = oracle.br_velocity(z[:, idx], z, gam, 1.0 / n**2, delta)
+    model = zm.ZModel(n, periodic=True, delta=delta, fp32c=fp32c)
+    u = model.velocity(z, w, want_wdot=False)
+    model.close()
+    e = rel(u[:, idx], u_ref)
+    print(f"256^2 sampled fp32c={fp32c}: rel L2 u={e:.3e}")
+    assert e <= (TOL32 if fp32c else TOL64)
+
+
+def test_full_size_sampled_512_fp32c(zm):
+    n = 512
+    z0, w0 = inputs.multi_mode(n, n_modes=8, seed=7, amp=0.02)
+    _, w = inputs.random_state(n, seed=12)
+    z = z0
+    delta = 0.1 / n
+    m = oracle.Mesh(n, periodic=True)
+    a1, a2, _, _ = oracle.geometry(m, z)
+    gam = oracle.sheet_strength(w, a1, a2)
+    idx = np.random.default_rng(6).choice(n * n, 256, replace=False)
+    u_ref = oracle.br_velocity(z[:, idx], z, gam, 1.0 / n**2, delta)
+    model = zm.ZModel(n, periodic=True, atwood=0.7, delta=delta, fp32c=True)
+    u = model.velocity(z, w, want_wdot=False)
+    model.close()
+    e = rel(u[:, idx], u_ref)
+    print(f"512^2 sampled fp32c: rel L2 u={e:.3e}")
+    assert e <= TOL32
+
+
+def test_low_order_1024_full(zm):
+    n = 1024
+    z, _ = inputs.multi_mode(n, n_modes=8, seed=7, amp=0.02)
+    _, w = inputs.random_state(n, seed=13)
+    m = oracle.Mesh(n, periodic=True)
+    u_ref, wd_ref = oracle.derivative(m, z, w, 0.7, 1.0, 0.0, 0.0, order=oracle.ORDER_LOW)
+    model = zm.ZModel(n, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW)
+    u, wd = model.velocity(z, w)
+    model.close()
+    eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+    print(f"low order 1024^2: rel L2 u={eu:.3e} wdot={ew:.3e}")
+    assert eu <= TOL64 and ew <= TOL64
+
+
+def test_deterministic_and_device_pointers(zm):
+    import torch
+    n = 48
+    z, w = inputs.random_state(n, seed=21)
+    for fp32c in (False, True):
+        model = zm.ZModel(n, periodic=True, fp32c=fp32c)
+        u1, wd1 = model.velocity(z, w)
+        zd = torch.from_numpy(z).cuda()
+        wdv = torch.from_numpy(w).cuda()
+        ud = torch.empty((3, n * n), dtype=torch.float64, device="cuda")
+        wdd = torch.empty((2, n * n), dtype=torch.float64, device="cuda")
+        zm.zm_set_stream(model.h, torch.cuda.current_stream().cuda_stream)
+        zm.zm_velocity(model.h, zd, wdv, ud, wdd)
+        torch.cuda.synchronize()
+        model.close()
+        assert np.array_equal(ud.cpu().numpy(), u1) and np.array_equal(wdd.cpu().numpy(), wd1)
+
+
+def test_invalid_arguments(zm):
+    with pytest.raises(zm.ZMError) as e:
+        zm.zm_create(4, 4)
+    assert e.value.code == zm.ZM_ERR_INVALID
+    with pytest.raises(zm.ZMError) as e:
+        zm.zm_create(32, 32, delta=0.0)
+    assert e.value.code == zm.ZM_ERR_INVALID
+    with pytest.raises(zm.ZMError) as e:
+        zm.zm_create(32, 32, periodic=False, order=zm.ZM_ORDER_LOW)
+    assert e.value.code == zm.ZM_ERR_UNSUPPORTED
+    with pytest.raises(zm.ZMError) as e:
+        zm.zm_create(48, 48, periodic=True, order=zm.ZM_ORDER_LOW)
+    assert e.value.code == zm.ZM_ERR_UNSUPPORTED
+    with pytest.raises(zm.ZMError) as e:
+        zm.zm_create(32, 32, order=zm.ZM_ORDER_MEDIUM)
+    assert e.value.code == zm.ZM_ERR_UNSUPPORTED
+
+
+def test_nonfinite_detection(zm):
+    n = 16
+    z, w = inputs.random_state(n, seed=2)
+    w[0, 5] = np.nan
+    model = zm.ZModel(n, periodic=True)
+    model.set_state(z, w)
+    assert zm.zm_check_finite(model.h) == zm.ZM_ERR_NONFINITE
+    w[0, 5] = 0.0
+    model.set_state(z, w)
+    assert zm.zm_check_finite(model.h) == zm.ZM_OK
+    model.close()

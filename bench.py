@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark: Z-Model high-order steps on one GB300 (and replicas on N GPUs).
+
+Workload (one "step" = one SSP-RK3 step = three derivative evaluations, each running the
+geometry pass, the all-pairs Birkhoff-Rott sum, the split reduction and the vorticity/RK3
+pass): the 256 x 256 periodic multi-mode interface (65,536 points; z3 = sum of 16 modes with
+integer (kx, ky) in [2, 8], amplitudes N(0, 0.01), phases U[0, 2 pi) from seed 0; w = 0;
+A = 0.5, g = 1, delta = 0.1 dx, dt = 1e-3) with FP32-compensated Birkhoff-Rott pair terms.
+Each step evaluates 3 x 65536^2 = 1.29e10 pair interactions.
+
+Also measured and reported beside the headline (not the headline):
+  * the plain FP64 form of the same step (the comparator);
+  * the low-order 1024 x 1024 FFT Riesz step (8 modes, amplitude 0.02, A = 0.7);
+  * the 32 x 32 single-mode FP64 step (launch bound).
+
+`--impl reference` times the CPU oracle (test infrastructure) on a bounded sample of the same
+workload and metric, on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BR G-pair-interactions/s & Z-Model steps/s vs plain FP64; serve p50/p99 ms"
+UNIT = "Gpair/s"
+N_SIDE = 256
+FLOPS_PER_PAIR = 26  # direct-formula FP32 flops per pair interaction (FMA = 2; rsqrt on MUFU)
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+CONFIG = {"workload": "multimode-256x256-highorder-fp32c", "n_side": N_SIDE, "points": N_SIDE**2,
+          "modes": 16, "order": "high", "precision": "fp32c",
+          "pairs_per_step": 3 * N_SIDE**4, "l2": "flushed between timed steps (256 MB write)"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / low-order / 32^2 side runs")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    p = os.path.join(ROOT, "paper_2406_05490_gb300", "csrc", "zm_br.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per Birkhoff-Rott launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "br_fp32c_traffic.json")
+    try:
+        d = json.load(open(p))
+        if d.get("source_sha256_16") == kernel_source_hash():
+            return d.get("dram_bytes_per_launch_full_size")
+    except Exception:
+        pass
+    return None
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "gb300" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, x, device=None):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle arm
+# ---------------------------------------------------------------------------------------------
+
+def oracle_sample_rate(n_targets=1024, seed=0):
+    """The oracle's Birkhoff-Rott sum on a bounded sample of the 256^2 workload: n_targets
+    seeded targets against all 65,536 sources (geometry and sheet strength computed by the
+    oracle on the full mesh first).  Returns (pairs/s, seconds, sample description)."""
+    import numpy as np
+
+    import oracle
+    from paper_2406_05490_gb300 import inputs
+    n = N_SIDE
+    z, w = inputs.multi_mode(n, n_modes=16, seed=0)
+    # the first stage has w = 0 (gamma = 0); a smooth non-zero w gives the same work per pair
+    _, w = inputs.random_state(n, seed=1)
+    m = oracle.Mesh(n, periodic=True)
+    a1, a2, _, _ = oracle.geometry(m, z)
+    gam = oracle.sheet_strength(w, a1, a2)
+    idx = np.random.default_rng(seed).choice(n * n, n_targets, replace=False)
+    t0 = time.perf_counter()
+    oracle.br_velocity(z[:, idx], z, gam, 1.0 / n**2, 0.1 / n)
+    dt = time.perf_counter() - t0
+    pairs = n_targets * n * n
+    return pairs / dt, dt, (f"{n_targets} seeded targets x all {n*n} sources of the 256^2 interface, "
+                            "one Birkhoff-Rott evaluation of the oracle (serial FP64, 1 core)")
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    # each step: one bounded sample (256 targets x 65,536 sources)
+    for _ in range(args.warmup):
+        oracle_sample_rate(64)
+    pairs, secs = 0, 0.0
+    sample = ""
+    for k in range(args.steps):
+        r, dt, sample = oracle_sample_rate(256, seed=k)
+        pairs += r * dt
+        secs += dt
+    value = pairs / secs / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": dict(CONFIG, parallelism="replicas x1"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: " + sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+
+def timed_steps(model, zm, torch, steps, warmup, flush, profile=True):
+    """Device time of `steps` RK3 steps (CUDA events on the context's stream, L2 flushed
+    between steps, flush excluded).  Returns (ms_total, profile dict)."""
+    stream = torch.cuda.current_stream()
+    zm.zm_set_stream(model.h, stream.cuda_stream)
+    for _ in range(warmup):
+        model.step(1e-3, 1)
+    torch.cuda.synchronize()
+    zm.zm_set_profiling(model.h, 1 if profile else 0)
+    zm.zm_reset_profile(model.h)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        model.step(1e-3, 1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    prof = zm.zm_get_profile(model.h)
+    zm.zm_set_profiling(model.h, 0)
+    return ms, prof
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_2406_05490_gb300 import inputs, zm
+    zm.load()
+    dev = torch.device("cuda", local)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    n = N_SIDE
+    N = n * n
+    z0, w0 = inputs.multi_mode(n, n_modes=16, seed=rank)
+    model = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, fp32c=True)
+    model.set_state(z0, w0)
+
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms, prof = timed_steps(model, zm, torch, args.steps, args.warmup, flush)
+    barrier(ws)
+    torch.cuda.synchronize()
+    ms_max = allmax(ws, ms, dev)
+    pairs_per_step = 3 * N * N
+    value = ws * pairs_per_step * args.steps / (ms_max * 1e-3) / 1e9
+    steps_per_s = args.steps / (ms_max * 1e-3)
+    launches = sum(prof["launches"].values())
+
+    # roofline of the dominant kernel (Birkhoff-Rott sum): ALU bound, FP32
+    br_ms = prof["ms"]["br"] / max(prof["launches"]["br"], 1)
+    achieved = FLOPS_PER_PAIR * N * N / (br_ms * 1e-3) / 1e12
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = recorded_traffic()
+
+    # end to end through the C ABI with host buffers: H2D state in, one step, D2H state out
+    zh = np.ascontiguousarray(z0)
+    wh = np.ascontiguousarray(w0)
+    try:
+        zp = torch.from_numpy(zh).pin_memory()
+        wp = torch.from_numpy(wh).pin_memory()
+        zo = torch.empty_like(zp).pin_memory()
+        wo = torch.empty_like(wp).pin_memory()
+    except Exception:
+        zp, wp, zo, wo = torch.from_numpy(zh), torch.from_numpy(wh), torch.empty(3, N, dtype=torch.float64), torch.empty(2, N, dtype=torch.float64)
+    e2e_model = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, fp32c=True)
+    e2e_steps = max(3, min(args.steps, 10))
+    for k in range(e2e_steps + 1):
+        if k == 1:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        zm.zm_set_state(e2e_model.h, zp, wp)
+        zm.zm_step(e2e_model.h, 1e-3, 1)
+        zm.zm_get_state(e2e_model.h, zo, wo)  # host pointers: returns after the copy
+    e2e_s = time.perf_counter() - t0
+    e2e_s = allmax(ws, e2e_s, dev)
+    e2e_model.close()
+    e2e_value = ws * pairs_per_step * e2e_steps / e2e_s / 1e9
+
+    extras = {}
+    if not args.no_extras:
+        # plain FP64 comparator: the same interface, FP64 pair terms
+        m64 = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, fp32c=False)
+        m64.set_state(z0, w0)
+        k64 = 2
+        ms64, prof64 = timed_steps(m64, zm, torch, k64, 1, flush)
+        m64.close()
+        extras["fp64_plain"] = {"gpairs_per_s": pairs_per_step * k64 / (ms64 * 1e-3) / 1e9,
+                                "steps_per_s": k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64,
+                                "steps": k64}
+        extras["fp32c_speedup_vs_fp64"] = value / ws / extras["fp64_plain"]["gpairs_per_s"]
+        # low-order 1024^2 FFT Riesz step
+        nl = 1024
+        zl, wl = inputs.multi_mode(nl, n_modes=8, seed=7, amp=0.02)
+        ml = zm.ZModel(nl, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW)
+        ml.set_state(zl, wl)
+        kl = 10
+        msl, profl = timed_steps(ml, zm, torch, kl, 3, flush)
+        ml.close()
+        nfft = max(profl["launches"]["fft"] // 3, 1)
+        fft_ms = profl["ms"]["fft"] / nfft
+        extras["low_order_1024"] = {
+            "steps_per_s": kl / (msl * 1e-3), "ms_per_step": msl / kl,
+            "riesz_ms_per_eval": fft_ms,
+            # algorithmic bytes of one Riesz evaluation: read w (16 B/pt) + normal (24) + q (8),
+            # write u (24) + Phi (8)
+            "riesz_alg_gbs": 80 * nl * nl / (fft_ms * 1e-3) / 1e9,
+            "kernel_ms_per_step": {k: v / kl for k, v in profl["ms"].items()}}
+        # 32^2 single-mode FP64 (launch bound)
+        zs, wsn = inputs.single_mode(32)
+        ms_ = zm.ZModel(32, periodic=False, atwood=0.5, g=1.0, delta=0.1 / 32)
+        ms_.set_state(zs, wsn)
+        k1 = 10
+        ms1, _ = timed_steps(ms_, zm, torch, k1, 3, flush, profile=False)
+        ms_.close()
+        extras["single_mode_32_fp64"] = {"steps_per_s": k1 / (ms1 * 1e-3), "ms_per_step": ms1 / k1}
+
+    cpu = None
+    if rank == 0 and ws == 1:
+        rate, secs, sample = oracle_sample_rate(1024)
+        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds": secs}
+    model.close()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": dict(CONFIG, parallelism=f"replicas x{ws}"),
+        "steps_per_s": steps_per_s * 1.0,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "br32c",
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+                     "flops_per_pair": FLOPS_PER_PAIR, "br_ms_per_launch": br_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 5 * N * 8,
+                "d2h_bytes_per_step": 5 * N * 8},
+        "gpu_launches": launches,
+        "kernel_ms": prof["ms"], "kernel_launches": prof["launches"],
+        "clocks": clk.summary(),
+    }
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

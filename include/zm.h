@@ -141,6 +141,37 @@ int zm_check_finite(zm_ctx *ctx);
  * 2 flops), 1: FP64 FMA flop/s, 2: MUFU rsqrt operations/s.  Synchronous; allocates 64 bytes. */
 int zm_measure_peak(int kind, double *ops_per_s);
 
+/* ---- Birkhoff-Rott sum without allocation ------------------------------------------------ */
+
+/* The paper has no counterpart: this entry point exists for callers that cannot allocate GPU
+ * memory -- a host application that reserves all device memory at start-up and forbids later
+ * allocations, or code that must not pay the device-wide synchronisation that cudaMalloc and
+ * cudaFree imply.  It computes the FP64 all-pairs sum of zm_velocity's high-order path on
+ * caller-prepared inputs and allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * call.  Its workspace (tile-major source records, split partial sums, a status word; 9 MiB in
+ * all) is one static device array inside libzm.so, held by every GPU that loads the library
+ * until the process exits.
+ *
+ *   u_i = sum_j (z_j - z_i) x gamma_j / (|z_j - z_i|^2 + delta^2)^(3/2),  i, j < n
+ *
+ * n      number of points, 1 <= n <= 65536 (the workspace limit); larger n -> ZM_ERR_INVALID.
+ * z      device, 3n doubles, component-major positions (z1[0..n), z2[0..n), z3[0..n)).
+ * gamma  device, 3n doubles, component-major scaled sheet strengths; for a mesh these are
+ *        (dx1 dx2 / 4 pi)(w1 a2 - w2 a1), which makes u the high-order velocity.
+ * delta  core size, > 0.
+ * u      device, 3n doubles, output.
+ * status optional device int32: set to ZM_OK, or ZM_ERR_TIMEOUT if a bounded device-side wait
+ *        gave up, when the work completes.  May be NULL.
+ * cuda_stream  the cudaStream_t to run on (NULL: legacy default stream).
+ * Asynchronous on cuda_stream; returns ZM_ERR_INVALID for bad sizes, null or host pointers.
+ * The first call on each device looks up the workspace's device address (cudaGetSymbolAddress
+ * with that device current) and caches it; make that first call before any stream capture.
+ * All calls in the process share the one workspace: it keeps the last call's contents, every
+ * call rewrites what it reads before reading it, and calls whose work overlaps on the GPU
+ * (different streams, or different host threads without ordering) race on it. */
+int zm_br_velocity_noalloc(int32_t n, const double *z, const double *gamma, double delta,
+                           double *u, int32_t *status, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

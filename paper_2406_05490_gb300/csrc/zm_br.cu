@@ -19,6 +19,8 @@
 //          differences accurate to FP32 relative precision; pair terms in FP32 with one MUFU
 //          rsqrt; per-tile FP32 partials; FP64 accumulation across tiles.
 #include <algorithm>
+#include <cmath>
+#include <mutex>
 
 #include "zm_internal.cuh"
 
@@ -276,3 +278,135 @@ int launch_br(zm_ctx *c, const double *y)
 }
 
 }  // namespace zm
+
+// ---- Birkhoff-Rott sum that allocates nothing ------------------------------------------------
+// A variant of the FP64 all-pairs sum for callers that cannot allocate device memory (for
+// example a host application that reserves all GPU memory up front and forbids allocation
+// afterwards, or code that must not trigger the device-wide synchronisation cudaMalloc and
+// cudaFree imply).  Its workspace -- the tile-major source records, the split partial sums and
+// a status word -- lives in one file-scope device array that every GPU loading this library
+// holds until the process exits.
+
+namespace zm {
+namespace {
+
+constexpr int kNaMaxN = 65536;                        // largest supported point count
+constexpr int kNaTs = kTile1 * kTile2;                // 256 sources per tile
+constexpr int kNaMaxTiles = kNaMaxN / kNaTs;          // 256
+constexpr int kNaSplits = 4;                          // source splits (partial sums)
+constexpr size_t kNaHead = 32;                        // 256 bytes: status word, padding
+constexpr size_t kNaRec = (size_t)kNaMaxTiles * kRec64 * kNaTs;   // 3 MiB of records
+constexpr size_t kNaPart = (size_t)kNaSplits * 3 * kNaMaxN;       // 6 MiB of partials
+constexpr size_t kNaDoubles = kNaHead + kNaRec + kNaPart;         // 9 MiB + 256 B in total
+
+}  // namespace
+}  // namespace zm
+
+static __device__ __align__(256) double zm_noalloc_scratch[zm::kNaDoubles];
+
+namespace zm {
+namespace {
+
+// Records for this call: every slot of every used tile is written (padding slots with zero
+// strength), so nothing left by an earlier call is read.  Also clears the status word.
+__global__ void na_pack_kernel(int n, int ntiles, const double *__restrict__ z,
+                               const double *__restrict__ gamma, double *__restrict__ rec,
+                               int *status)
+{
+    const size_t total = (size_t)ntiles * kRec64 * kNaTs;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int slot = (int)(e % kNaTs);
+        const int row = (int)((e / kNaTs) % kRec64);
+        const int tile = (int)(e / ((size_t)kNaTs * kRec64));
+        const int p = tile * kNaTs + slot;
+        double v = 0.0;
+        if (p < n) v = (row < 3) ? z[(size_t)row * n + p] : gamma[(size_t)(row - 3) * n + p];
+        rec[e] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
+}
+
+__global__ void na_reduce_kernel(int n, int nsplit, const double *__restrict__ part,
+                                 double *__restrict__ u, const int *status_in, int32_t *status_out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) {
+        double s[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < nsplit; ++k)
+            for (int c = 0; c < 3; ++c) s[c] += part[((size_t)k * 3 + c) * n + p];
+        for (int c = 0; c < 3; ++c) u[(size_t)c * n + p] = s[c];
+    }
+    if (status_out && p == 0) *status_out = (*status_in & kErrTimeout) ? ZM_ERR_TIMEOUT : ZM_OK;
+}
+
+std::mutex g_na_mutex;
+constexpr int kNaMaxDevices = 64;
+double *g_na_base[kNaMaxDevices];  // device address of zm_noalloc_scratch, per device
+
+// Once per device, with that device current: look up the array's device address.  In host
+// code the symbol names a host-side shadow, never the device memory itself.
+int na_scratch(double **out)
+{
+    int dev = -1;
+    int rc = cuda_check(cudaGetDevice(&dev), "zm_br_velocity_noalloc: cudaGetDevice");
+    if (rc) return rc;
+    if (dev < 0 || dev >= kNaMaxDevices)
+        return set_error(ZM_ERR_UNSUPPORTED, "zm_br_velocity_noalloc: device ordinal above 63");
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_base[dev]) {
+        void *p = nullptr;
+        rc = cuda_check(cudaGetSymbolAddress(&p, zm_noalloc_scratch),
+                        "zm_br_velocity_noalloc: cudaGetSymbolAddress");
+        if (rc) return rc;
+        g_na_base[dev] = static_cast<double *>(p);
+    }
+    *out = g_na_base[dev];
+    return ZM_OK;
+}
+
+bool on_device(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace zm
+
+extern "C" int zm_br_velocity_noalloc(int32_t n, const double *z, const double *gamma,
+                                      double delta, double *u, int32_t *status,
+                                      void *cuda_stream)
+{
+    using namespace zm;
+    if (n < 1 || n > kNaMaxN)
+        return set_error(ZM_ERR_INVALID,
+                         "zm_br_velocity_noalloc: n must be in [1, 65536] (size of the static workspace)");
+    if (!z || !gamma || !u || !(delta > 0) || !std::isfinite(delta))
+        return set_error(ZM_ERR_INVALID, "zm_br_velocity_noalloc: null pointer or delta <= 0");
+    if (!on_device(z) || !on_device(gamma) || !on_device(u) || (status && !on_device(status)))
+        return set_error(ZM_ERR_INVALID, "zm_br_velocity_noalloc: z, gamma, u, status must be device memory");
+    double *base = nullptr;
+    int rc = na_scratch(&base);
+    if (rc) return rc;
+    int *flag = reinterpret_cast<int *>(base);
+    double *rec = base + kNaHead;
+    double *part = rec + kNaRec;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+    const int ntiles = (n + kNaTs - 1) / kNaTs;
+    const int tps = (ntiles + kNaSplits - 1) / kNaSplits;
+    const int nsplit = (ntiles + tps - 1) / tps;
+    na_pack_kernel<<<std::min(1024, (ntiles * kRec64 * kNaTs + 255) / 256), 256, 0, s>>>(
+        n, ntiles, z, gamma, rec, flag);
+    const int per_cta = kTpb64 * kR64;
+    dim3 grid((n + per_cta - 1) / per_cta, nsplit);
+    br64_kernel<kTpb64, kR64, kNaTs><<<grid, kTpb64, 0, s>>>(n, z, rec, ntiles, tps, delta * delta,
+                                                             part, flag);
+    na_reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, nsplit, part, u, flag, status);
+    return cuda_check(cudaGetLastError(), "zm_br_velocity_noalloc: launch");
+}

@@ -86,6 +86,7 @@ def load():
             "zm_reset_profile": (I, [VP]),
             "zm_check_finite": (I, [VP]),
             "zm_measure_peak": (I, [I, ctypes.POINTER(D)]),
+            "zm_br_velocity_noalloc": (I, [ctypes.c_int32, VP, VP, D, VP, VP, VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -190,6 +191,13 @@ def zm_measure_peak(kind):
     v = ctypes.c_double()
     _check(load().zm_measure_peak(int(kind), ctypes.byref(v)))
     return v.value
+
+
+def zm_br_velocity_noalloc(n, z, gamma, delta, u, status=None, stream=None):
+    """FP64 all-pairs sum on caller-owned device buffers; the library allocates nothing (its
+    workspace is a static device array, shared by all calls; n <= 65536)."""
+    _check(load().zm_br_velocity_noalloc(int(n), ptr(z), ptr(gamma), float(delta), ptr(u),
+                                         None if status is None else status.data_ptr(), stream))
 
 
 # ---- a small convenience wrapper -------------------------------------------------------------

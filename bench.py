@@ -106,7 +106,7 @@ class ClockSampler:
 
 
 def kernel_source_hash():
-    p = os.path.join(ROOT, "paper_2406_05490_gb300", "csrc", "zm_br.cu")
+    p = os.path.join(ROOT, "paper_2406_05490_gb300", "csrc", "zm_br32.cu")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
@@ -342,7 +342,7 @@ def run_gb300(args):
         "config": dict(CONFIG, parallelism=f"replicas x{ws}"),
         "steps_per_s": steps_per_s * 1.0,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "br32c",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "br32_kernel",
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
                      "flops_per_pair": FLOPS_PER_PAIR, "br_ms_per_launch": br_ms},
         "cpu_baseline": cpu,

@@ -138,7 +138,9 @@ int zm_check_finite(zm_ctx *ctx);
 
 /* Measure a CUDA-core throughput of the current GPU with CUDA events (the roofline denominator
  * of the Birkhoff-Rott kernels; the paper has no counterpart).  kind 0: FP32 FMA flop/s (FMA =
- * 2 flops), 1: FP64 FMA flop/s, 2: MUFU rsqrt operations/s.  Synchronous; allocates 64 bytes. */
+ * 2 flops), 1: FP64 FMA flop/s, 2: MUFU rsqrt operations/s, 3: packed FP32x2 FMA flop/s
+ * (fma.rn.f32x2), 4: packed and scalar FP32 FMAs interleaved, flop/s.  Synchronous; allocates
+ * 64 bytes. */
 int zm_measure_peak(int kind, double *ops_per_s);
 
 /* ---- Birkhoff-Rott sum without allocation ------------------------------------------------ */

@@ -79,6 +79,7 @@ int derivative(zm_ctx *c, const double *y)
     int rc = launch_geometry(c, y);
     if (rc) return rc;
     if (c->order == ZM_ORDER_LOW) return launch_riesz(c, y);
+    if (c->fp32c) return launch_br32(c);
     rc = launch_br(c, y);
     if (rc) return rc;
     return launch_reduce(c);
@@ -162,7 +163,7 @@ void zm_destroy(zm_ctx *c)
     }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     void *bufs[] = {c->y0, c->ya, c->yb, c->u, c->phi, c->q, c->nrm, c->src, c->part,
-                    c->fa, c->fb, c->tw1, c->tw2, c->err, c->flag};
+                    c->fa, c->fb, c->tw1, c->tw2, c->err, c->flag, c->src_far, c->tinfo};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (prev >= 0) cudaSetDevice(prev);
@@ -237,13 +238,23 @@ int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double de
               alloc((void **)&c->flag, sizeof(int));
     if (ok && ord == ZM_ORDER_HIGH) {
         c->tiling = make_tiling(G);
-        c->plan = plan_br(G, c->tiling, fp32c, sms);
-        const size_t rec = fp32c ? kRec32 * sizeof(float) : kRec64 * sizeof(double);
-        c->src_bytes = (size_t)c->tiling.ntiles * c->tiling.ts * rec;
-        ok = alloc(&c->src, c->src_bytes) &&
-             alloc((void **)&c->part, (size_t)c->plan.nsplit * 3 * N * sizeof(double));
+        const size_t slots = (size_t)c->tiling.ntiles * c->tiling.ts;
+        size_t part_doubles;
+        if (fp32c) {
+            c->plan32 = plan_br32(G, c->tiling, sms);
+            c->src_bytes = slots * kRec32 * sizeof(float);
+            part_doubles = c->plan32.part_doubles;
+            ok = alloc((void **)&c->src_far, slots * kRec32F * sizeof(float)) &&
+                 alloc((void **)&c->tinfo, c->tiling.ntiles * sizeof(float4));
+        } else {
+            c->plan = plan_br(G, c->tiling, sms);
+            c->src_bytes = slots * kRec64 * sizeof(double);
+            part_doubles = (size_t)c->plan.nsplit * 3 * N;
+        }
+        ok = ok && alloc(&c->src, c->src_bytes) && alloc((void **)&c->part, part_doubles * sizeof(double));
         // padding slots of edge tiles stay zero for good: zero strength, no contribution
         if (ok) ok = cudaMemset(c->src, 0, c->src_bytes) == cudaSuccess;
+        if (ok && fp32c) ok = init_far_records(c) == ZM_OK;
     }
     if (ok && ord == ZM_ORDER_LOW) ok = alloc((void **)&c->nrm, 3 * N * sizeof(double));
     if (ok) ok = cudaMemset(c->err, 0, sizeof(int)) == cudaSuccess &&

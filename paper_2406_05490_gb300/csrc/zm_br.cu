@@ -13,11 +13,9 @@
 // memory.  Split partial sums go to a [nsplit][3][N] workspace reduced in a fixed order by the
 // reduction kernel, which keeps results deterministic.
 //
-// Precision variants:
-//   FP64:  every operation in FP64 (rsqrt from CUDA's double-precision math library).
-//   FP32C: positions as FP32 hi/lo pairs, so r = (zh_j - zh_i) + (zl_j - zl_i) keeps near-pair
-//          differences accurate to FP32 relative precision; pair terms in FP32 with one MUFU
-//          rsqrt; per-tile FP32 partials; FP64 accumulation across tiles.
+// This file holds the FP64 variant (every operation in FP64, rsqrt from CUDA's double-precision
+// math library) -- the plain per-instance comparator -- and its allocation-free form; the
+// FP32-compensated variant is in zm_br32.cu.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -117,113 +115,7 @@ __global__ void __launch_bounds__(kTpb)
     }
 }
 
-template <int kTpb, int kR, int kTs>
-__global__ void __launch_bounds__(kTpb)
-    br32c_kernel(int N, const double *__restrict__ z, const float *__restrict__ src, int ntiles,
-                 int tiles_per_split, float d2, double *__restrict__ part, int *err)
-{
-    constexpr uint32_t kBytes = kRec32 * kTs * sizeof(float);
-    __shared__ __align__(128) float sh[2][kRec32 * kTs];
-    __shared__ __align__(8) uint64_t bar[2];
-
-    const int tid = threadIdx.x;
-    const int t0 = blockIdx.y * tiles_per_split;
-    const int nt = max(0, min(ntiles, t0 + tiles_per_split) - t0);
-
-    float hx[kR], hy[kR], hz[kR], lx[kR], ly[kR], lz[kR];
-    double ax[kR], ay[kR], az[kR];
-#pragma unroll
-    for (int r = 0; r < kR; ++r) {
-        const int p = min(blockIdx.x * kTpb * kR + r * kTpb + tid, N - 1);
-        const double x = z[p], y = z[(size_t)N + p], w = z[2 * (size_t)N + p];
-        hx[r] = __double2float_rn(x);
-        hy[r] = __double2float_rn(y);
-        hz[r] = __double2float_rn(w);
-        lx[r] = __double2float_rn(x - (double)hx[r]);
-        ly[r] = __double2float_rn(y - (double)hy[r]);
-        lz[r] = __double2float_rn(w - (double)hz[r]);
-        ax[r] = ay[r] = az[r] = 0.0;
-    }
-
-    if (tid == 0) {
-        dev::mbar_init(&bar[0], 1);
-        dev::mbar_init(&bar[1], 1);
-        dev::fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        for (int k = 0; k < 2 && k < nt; ++k)
-            dev::tma_load_1d(sh[k], src + (size_t)(t0 + k) * kRec32 * kTs, kBytes, &bar[k]);
-    }
-
-    int bad = 0, kb = 0;
-    for (int k = 0; k < nt; ++k) {
-        const int b = k & 1;
-        const bool ok = dev::mbar_wait_bounded(&bar[b], (k >> 1) & 1);
-        if (ok) {
-            const float *s = sh[b];
-            float px[kR], py[kR], pz[kR];
-#pragma unroll
-            for (int r = 0; r < kR; ++r) px[r] = py[r] = pz[r] = 0.0f;
-#pragma unroll 2
-            for (int jj = 0; jj < kTs; ++jj) {
-                const float shx = s[jj], shy = s[kTs + jj], shz = s[2 * kTs + jj];
-                const float slx = s[3 * kTs + jj], sly = s[4 * kTs + jj], slz = s[5 * kTs + jj];
-                const float gx = s[6 * kTs + jj], gy = s[7 * kTs + jj], gz = s[8 * kTs + jj];
-#pragma unroll
-                for (int r = 0; r < kR; ++r) {
-                    const float rx = (shx - hx[r]) + (slx - lx[r]);
-                    const float ry = (shy - hy[r]) + (sly - ly[r]);
-                    const float rz = (shz - hz[r]) + (slz - lz[r]);
-                    const float q = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, d2)));
-                    const float iq = dev::rsqrt_approx(q);
-                    const float kk = iq * iq * iq;
-                    px[r] = fmaf(kk, fmaf(ry, gz, -rz * gy), px[r]);
-                    py[r] = fmaf(kk, fmaf(rz, gx, -rx * gz), py[r]);
-                    pz[r] = fmaf(kk, fmaf(rx, gy, -ry * gx), pz[r]);
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < kR; ++r) {
-                ax[r] += (double)px[r];
-                ay[r] += (double)py[r];
-                az[r] += (double)pz[r];
-            }
-        }
-        bad = __syncthreads_or(!ok);
-        if (bad) {
-            kb = k;
-            break;
-        }
-        if (tid == 0 && k + 2 < nt) {
-            dev::fence_proxy_async();
-            dev::tma_load_1d(sh[b], src + (size_t)(t0 + k + 2) * kRec32 * kTs, kBytes, &bar[b]);
-        }
-    }
-    if (bad) {
-        if (tid == 0) {
-            atomicOr(err, kErrTimeout);
-            // let the copies still in flight (tiles kb and kb + 1) land, again with a bounded
-            // wait, before the CTA's shared memory is released
-            for (int k = kb; k < kb + 2 && k < nt; ++k)
-                (void)dev::mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1);
-        }
-        return;
-    }
-#pragma unroll
-    for (int r = 0; r < kR; ++r) {
-        const int p = blockIdx.x * kTpb * kR + r * kTpb + tid;
-        if (p < N) {
-            double *o = part + (size_t)blockIdx.y * 3 * N;
-            o[p] = ax[r];
-            o[(size_t)N + p] = ay[r];
-            o[2 * (size_t)N + p] = az[r];
-        }
-    }
-}
-
 constexpr int kTpb64 = 128, kR64 = 2;
-constexpr int kTpb32 = 256, kR32 = 4;
 
 }  // namespace
 
@@ -239,11 +131,11 @@ Tiling make_tiling(const Geom &g)
     return t;
 }
 
-BrPlan plan_br(const Geom &g, const Tiling &t, int fp32c, int sm_count)
+BrPlan plan_br(const Geom &g, const Tiling &t, int sm_count)
 {
     BrPlan p;
-    p.tpb = fp32c ? kTpb32 : kTpb64;
-    p.r = fp32c ? kR32 : kR64;
+    p.tpb = kTpb64;
+    p.r = kR64;
     const int per_cta = p.tpb * p.r;
     p.ntb = (g.N + per_cta - 1) / per_cta;
     // aim for about four resident CTAs per SM over the whole grid
@@ -262,16 +154,9 @@ int launch_br(zm_ctx *c, const double *y)
     dim3 grid(p.ntb, p.nsplit);
     cudaEvent_t ev = nullptr;
     prof_begin(c, ZM_K_BR, &ev);
-    const double d2 = c->delta * c->delta;
-    if (c->fp32c) {
-        br32c_kernel<kTpb32, kR32, kTile1 * kTile2><<<grid, kTpb32, 0, c->stream>>>(
-            g.N, y, static_cast<const float *>(c->src), c->tiling.ntiles, p.tiles_per_split,
-            (float)d2, c->part, c->err);
-    } else {
-        br64_kernel<kTpb64, kR64, kTile1 * kTile2><<<grid, kTpb64, 0, c->stream>>>(
-            g.N, y, static_cast<const double *>(c->src), c->tiling.ntiles, p.tiles_per_split, d2,
-            c->part, c->err);
-    }
+    br64_kernel<kTpb64, kR64, kTile1 * kTile2><<<grid, kTpb64, 0, c->stream>>>(
+        g.N, y, static_cast<const double *>(c->src), c->tiling.ntiles, p.tiles_per_split,
+        c->delta * c->delta, c->part, c->err);
     prof_end(c, ZM_K_BR, ev);
     c->prof.pairs += (int64_t)g.N * (int64_t)g.N;
     return cuda_check(cudaGetLastError(), "Birkhoff-Rott kernel launch");

@@ -28,9 +28,12 @@ struct Tiling {
 };
 
 // FP64 record: rows 0-2 absolute position, rows 3-5 scaled sheet strength -> [tile][6][ts] double
-// FP32C record: rows 0-2 position hi, 3-5 position lo, 6-8 scaled strength -> [tile][9][ts] float
+// FP32C near record: rows 0-2 position hi, 3-5 position lo, 6-8 scaled strength -> [tile][9][ts]
+// FP32C far record: rows 0-2 s = z - c_T (tile centre), 3 |s|^2 + delta^2, 4-6 scaled strength,
+//   7-9 s x strength -> [tile][10][ts] float
 constexpr int kRec64 = 6;
 constexpr int kRec32 = 9;
+constexpr int kRec32F = 10;
 
 // Launch geometry of the all-pairs kernel.
 struct BrPlan {
@@ -39,6 +42,14 @@ struct BrPlan {
     int nsplit;     // source splits (grid.y); partial sums reduced by a second kernel
     int tiles_per_split;
     int ntb;        // target blocks (grid.x)
+};
+
+// Launch plan of the FP32C Birkhoff-Rott kernel (persistent, stream-K ranges).
+struct Br32Plan {
+    int ctas;           // persistent CTAs (grid size)
+    int kseg;           // most target-group segments one CTA's range can touch
+    int occupancy;      // resident CTAs per SM
+    size_t part_doubles;
 };
 
 // Device-side status word bits.
@@ -67,7 +78,10 @@ struct zm_ctx {
     zm::BrPlan plan;
     void *src;
     size_t src_bytes;
-    double *part;  // [nsplit][3][N]
+    double *part;  // FP64: [nsplit][3][N]; FP32C: [ctas * kseg][3][512]
+    float *src_far;   // FP32C far records
+    float4 *tinfo;    // FP32C per-tile bounding sphere: centre, radius
+    zm::Br32Plan plan32;
 
     // low order: FFT workspace (complex doubles) and twiddles
     double2 *fa, *fb, *tw1, *tw2;
@@ -109,9 +123,14 @@ int launch_reduce(zm_ctx *c);
 int check_finite(zm_ctx *c, const double *y, size_t n, int *dev_flag);
 
 // ---- Birkhoff-Rott kernels (zm_br.cu) ----------------------------------------------------------
-BrPlan plan_br(const Geom &g, const Tiling &t, int fp32c, int sm_count);
+BrPlan plan_br(const Geom &g, const Tiling &t, int sm_count);
 Tiling make_tiling(const Geom &g);
-int launch_br(zm_ctx *c, const double *y);
+int launch_br(zm_ctx *c, const double *y);  // FP64 path (then launch_reduce)
+
+// ---- FP32C Birkhoff-Rott kernels (zm_br32.cu) -----------------------------------------------------
+Br32Plan plan_br32(const Geom &g, const Tiling &t, int sm_count);
+int init_far_records(zm_ctx *c);
+int launch_br32(zm_ctx *c);  // sum + its reduction (u, Phi)
 
 // ---- low order (zm_fft.cu) ---------------------------------------------------------------------
 int fft_setup(zm_ctx *c);

@@ -46,6 +46,76 @@ __global__ void __launch_bounds__(kPeakTpb) dfma_probe(int iters, double a, doub
     if (s == 12345.678) sink[0] = s;
 }
 
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// packed FP32x2 FMA (two FMAs per lane per instruction)
+__global__ void __launch_bounds__(kPeakTpb) ffma2_probe(int iters, float a, float b, float *sink)
+{
+    unsigned long long x[kChains];
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+    const unsigned long long ua = *reinterpret_cast<const unsigned long long *>(&a2);
+    const unsigned long long ub = *reinterpret_cast<const unsigned long long *>(&b2);
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) {
+        float2 v = make_float2(threadIdx.x * 1e-3f + k, threadIdx.x * 2e-3f + k);
+        x[k] = *reinterpret_cast<unsigned long long *>(&v);
+    }
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) x[k] = ffma2(x[k], ua, ub);
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) {
+        float2 v = *reinterpret_cast<float2 *>(&x[k]);
+        s += v.x + v.y;
+    }
+    if (s == 12345.678f) sink[0] = s;
+}
+
+// packed FP32x2 FMA chains interleaved with scalar FMA chains (4 + 4): shows whether scalar
+// FMAs run beside packed ones
+__global__ void __launch_bounds__(kPeakTpb) mixed_probe(int iters, float a, float b, float *sink)
+{
+    unsigned long long x[kChains / 2];
+    float y[kChains / 2];
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+    const unsigned long long ua = *reinterpret_cast<const unsigned long long *>(&a2);
+    const unsigned long long ub = *reinterpret_cast<const unsigned long long *>(&b2);
+#pragma unroll
+    for (int k = 0; k < kChains / 2; ++k) {
+        float2 v = make_float2(threadIdx.x * 1e-3f + k, threadIdx.x * 2e-3f + k);
+        x[k] = *reinterpret_cast<unsigned long long *>(&v);
+        y[k] = threadIdx.x * 3e-3f + k;
+    }
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+#pragma unroll
+            for (int k = 0; k < kChains / 2; ++k) {
+                x[k] = ffma2(x[k], ua, ub);
+                y[k] = fmaf(y[k], a, b);
+            }
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChains / 2; ++k) {
+        float2 v = *reinterpret_cast<float2 *>(&x[k]);
+        s += v.x + v.y + y[k];
+    }
+    if (s == 12345.678f) sink[0] = s;
+}
+
 __global__ void __launch_bounds__(kPeakTpb) rsqrt_probe(int iters, float *sink)
 {
     float x[kChains];
@@ -71,7 +141,7 @@ using namespace zm;
 
 extern "C" int zm_measure_peak(int kind, double *ops_per_s)
 {
-    if (!ops_per_s || kind < 0 || kind > 2) return set_error(ZM_ERR_INVALID, "zm_measure_peak: bad argument");
+    if (!ops_per_s || kind < 0 || kind > 4) return set_error(ZM_ERR_INVALID, "zm_measure_peak: bad argument");
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -87,7 +157,9 @@ extern "C" int zm_measure_peak(int kind, double *ops_per_s)
         cudaEventRecord(a);
         if (kind == 0) ffma_probe<<<blocks, kPeakTpb>>>(iters, 0.999f, 1e-3f, (float *)sink);
         else if (kind == 1) dfma_probe<<<blocks, kPeakTpb>>>(iters, 0.999, 1e-3, (double *)sink);
-        else rsqrt_probe<<<blocks, kPeakTpb>>>(iters, (float *)sink);
+        else if (kind == 2) rsqrt_probe<<<blocks, kPeakTpb>>>(iters, (float *)sink);
+        else if (kind == 3) ffma2_probe<<<blocks, kPeakTpb>>>(iters, 0.999f, 1e-3f, (float *)sink);
+        else mixed_probe<<<blocks, kPeakTpb>>>(iters, 0.999f, 1e-3f, (float *)sink);
         cudaEventRecord(b);
         cudaEventSynchronize(b);
         float ms = 0.f;
@@ -95,8 +167,10 @@ extern "C" int zm_measure_peak(int kind, double *ops_per_s)
         if (rep > 0 && ms < best) best = ms;
     }
     const double ops = (double)blocks * kPeakTpb * iters * 16.0 * kChains;
-    // FMA probes report flops (FMA = 2); the rsqrt probe reports operations
-    *ops_per_s = (kind == 2 ? 1.0 : 2.0) * ops / (best * 1e-3);
+    // FMA probes report flops (FMA = 2; a packed x2 FMA = 4; the mixed probe does one packed and
+    // one scalar FMA per chain pair = 6 flops per 2 chain steps); the rsqrt probe reports operations
+    const double per = (kind == 2) ? 1.0 : (kind == 3) ? 4.0 : (kind == 4) ? 3.0 : 2.0;
+    *ops_per_s = per * ops / (best * 1e-3);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaFree(sink);

@@ -53,7 +53,8 @@ __device__ __forceinline__ double diff2(const double v[5], double inv12dx2)
 template <bool kFp32c, bool kLow>
 __global__ void __launch_bounds__(kTpb)
     geometry_kernel(Geom g, Tiling t, const double *__restrict__ y, double pref, double grav,
-                    void *__restrict__ src, double *__restrict__ q, double *__restrict__ nrm)
+                    float d2f, void *__restrict__ src, float *__restrict__ far_rec,
+                    float4 *__restrict__ tinfo, double *__restrict__ q, double *__restrict__ nrm)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.N) return;
@@ -96,14 +97,44 @@ __global__ void __launch_bounds__(kTpb)
     const size_t tile = (size_t)ti * t.nt2 + tj;
     const int slot = (i - ti * t.tp1) * t.tp2 + (j - tj * t.tp2);
     if (kFp32c) {
+        // near record: hi/lo position and strength
         float *r = static_cast<float *>(src) + tile * kRec32 * t.ts + slot;
+        float gf[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const double zc = z[(size_t)c * g.N + p];
             const float hi = __double2float_rn(zc);
+            gf[c] = __double2float_rn(gm[c]);
             r[(size_t)c * t.ts] = hi;
             r[(size_t)(3 + c) * t.ts] = __double2float_rn(zc - (double)hi);
-            r[(size_t)(6 + c) * t.ts] = __double2float_rn(gm[c]);
+            r[(size_t)(6 + c) * t.ts] = gf[c];
+        }
+        // far record: position relative to the tile centre (the middle node of the tile's part
+        // of the mesh), |s|^2 + delta^2, strength and s x strength
+        const int h1 = min(t.tp1, g.n1 - ti * t.tp1), h2 = min(t.tp2, g.n2 - tj * t.tp2);
+        const size_t pc = (size_t)(ti * t.tp1 + h1 / 2) * g.n2 + (tj * t.tp2 + h2 / 2);
+        float cf[3], sf[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cf[c] = __double2float_rn(z[(size_t)c * g.N + pc]);
+            sf[c] = __double2float_rn(z[(size_t)c * g.N + p] - (double)cf[c]);
+        }
+        float *f = far_rec + tile * kRec32F * t.ts + slot;
+        f[0] = sf[0];
+        f[t.ts] = sf[1];
+        f[2 * (size_t)t.ts] = sf[2];
+        f[3 * (size_t)t.ts] = fmaf(sf[0], sf[0], fmaf(sf[1], sf[1], fmaf(sf[2], sf[2], d2f)));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[(size_t)(4 + c) * t.ts] = gf[c];
+        f[7 * (size_t)t.ts] = __double2float_rn((double)sf[1] * gf[2] - (double)sf[2] * gf[1]);
+        f[8 * (size_t)t.ts] = __double2float_rn((double)sf[2] * gf[0] - (double)sf[0] * gf[2]);
+        f[9 * (size_t)t.ts] = __double2float_rn((double)sf[0] * gf[1] - (double)sf[1] * gf[0]);
+        const float rad = sqrtf(sf[0] * sf[0] + sf[1] * sf[1] + sf[2] * sf[2]);
+        atomicMax(reinterpret_cast<unsigned int *>(&tinfo[tile].w), __float_as_uint(rad));
+        if ((size_t)p == pc) {
+            tinfo[tile].x = cf[0];
+            tinfo[tile].y = cf[1];
+            tinfo[tile].z = cf[2];
         }
     } else {
         double *r = static_cast<double *>(src) + tile * kRec64 * t.ts + slot;
@@ -202,15 +233,21 @@ int launch_geometry(zm_ctx *c, const double *y)
     cudaEvent_t ev = nullptr;
     prof_begin(c, ZM_K_GEOMETRY, &ev);
     const bool low = (c->order == ZM_ORDER_LOW);
-    if (low)
-        geometry_kernel<false, true><<<grid, kTpb, 0, c->stream>>>(g, c->tiling, y, pref, c->g,
-                                                                  nullptr, c->q, c->nrm);
-    else if (c->fp32c)
-        geometry_kernel<true, false><<<grid, kTpb, 0, c->stream>>>(g, c->tiling, y, pref, c->g,
-                                                                  c->src, c->q, nullptr);
-    else
-        geometry_kernel<false, false><<<grid, kTpb, 0, c->stream>>>(g, c->tiling, y, pref, c->g,
-                                                                   c->src, c->q, nullptr);
+    const float d2f = (float)(c->delta * c->delta);
+    if (low) {
+        geometry_kernel<false, true><<<grid, kTpb, 0, c->stream>>>(
+            g, c->tiling, y, pref, c->g, d2f, nullptr, nullptr, nullptr, c->q, c->nrm);
+    } else if (c->fp32c) {
+        // tile spheres are rebuilt every evaluation: radius by atomicMax from zero
+        int rc = cuda_check(cudaMemsetAsync(c->tinfo, 0, c->tiling.ntiles * sizeof(float4), c->stream),
+                            "tile-sphere reset");
+        if (rc) return rc;
+        geometry_kernel<true, false><<<grid, kTpb, 0, c->stream>>>(
+            g, c->tiling, y, pref, c->g, d2f, c->src, c->src_far, c->tinfo, c->q, nullptr);
+    } else {
+        geometry_kernel<false, false><<<grid, kTpb, 0, c->stream>>>(
+            g, c->tiling, y, pref, c->g, d2f, c->src, nullptr, nullptr, c->q, nullptr);
+    }
     prof_end(c, ZM_K_GEOMETRY, ev);
     return cuda_check(cudaGetLastError(), "geometry kernel launch");
 }

@@ -184,7 +184,7 @@ def zm_check_finite(h):
     return load().zm_check_finite(h)
 
 
-PEAK_FP32, PEAK_FP64, PEAK_RSQRT = 0, 1, 2
+PEAK_FP32, PEAK_FP64, PEAK_RSQRT, PEAK_FP32X2, PEAK_MIXED = 0, 1, 2, 3, 4
 
 
 def zm_measure_peak(kind):

@@ -61,8 +61,9 @@ extern "C" {
 #define ZM_ORDER_MEDIUM 1
 #define ZM_ORDER_HIGH 2
 #define ZM_PREC_FP64 0x000
-#define ZM_PREC_FP32C 0x100 /* BR pair terms in FP32 (hi/lo positions), per-tile FP32 partials,
-                               FP64 accumulation across tiles; everything else FP64 */
+#define ZM_PREC_FP32C 0x100 /* BR pair terms in FP32 (hi/lo positions near, tile-local
+                               coordinates far), per-tile FP32 partials, exact 64-bit fixed-point
+                               accumulation across tiles (finer than FP64); all else FP64 */
 
 typedef struct {
     int32_t n1, n2;   /* nodes along alpha1 (slow index i) and alpha2 (fast index j), >= 5 */
@@ -142,6 +143,41 @@ int zm_check_finite(zm_ctx *ctx);
  * (fma.rn.f32x2), 4: packed and scalar FP32 FMAs interleaved, flop/s.  Synchronous; allocates
  * 64 bytes. */
 int zm_measure_peak(int kind, double *ops_per_s);
+
+/* ---- batches of interfaces (high order, FP32C) ------------------------------------------- */
+
+/* Many independent interfaces of uneven mesh sizes advanced together: each RK3 stage runs four
+ * launches over the whole batch (geometry, one persistent all-pairs launch over a shared work
+ * list, the fixed-point finish, the vorticity/RK3 pass) and a whole step is replayed from a
+ * CUDA graph.  Per-interface results are bitwise independent of the other interfaces in the
+ * batch and of scheduling (exact fixed-point accumulation), and equal to those of zm_create
+ * with ZM_ORDER_HIGH | ZM_PREC_FP32C.  The paper has no batched form: it runs one interface
+ * over many ranks (Sec. 3). */
+typedef struct zm_batch zm_batch;
+
+/* count interfaces; meshes[k], atwood[k] and delta[k] (> 0) per interface, g and mu shared.
+ * Sides >= 5, n1 * n2 <= 2^24 each.  Allocates all device state (owned until destroy). */
+int zm_batch_create(int32_t count, const zm_mesh *meshes, const double *atwood, double g,
+                    double mu, const double *delta, zm_batch **out);
+int zm_batch_set_stream(zm_batch *b, void *cuda_stream);
+/* State of interface `index` in or out (host or device pointers, layout as for zm_set_state). */
+int zm_batch_set_state(zm_batch *b, int32_t index, const double *z, const double *w);
+int zm_batch_get_state(zm_batch *b, int32_t index, double *z, double *w);
+/* One derivative evaluation of every interface at its resident state (asynchronous); then
+ * zm_batch_get_velocity copies interface `index`'s u (3N) and dw/dt (2N; either may be NULL). */
+int zm_batch_velocity(zm_batch *b);
+int zm_batch_get_velocity(zm_batch *b, int32_t index, double *u, double *wdot);
+/* nsteps SSP-RK3 steps of every interface (asynchronous; one graph launch per step). */
+int zm_batch_step(zm_batch *b, double dt, int32_t nsteps);
+int zm_batch_sync(zm_batch *b);
+/* Tuning: source tiles per all-pairs work item (0 = default by size); results do not change. */
+int zm_batch_set_chunk(zm_batch *b, int32_t chunk);
+/* Totals: mesh points, pair interactions per evaluation, work items, persistent CTAs. */
+int zm_batch_info(zm_batch *b, int64_t *points, int64_t *pairs_per_eval, int64_t *work_items,
+                  int32_t *ctas);
+int zm_batch_set_profiling(zm_batch *b, int on);
+int zm_batch_get_profile(zm_batch *b, zm_profile *out);
+void zm_batch_destroy(zm_batch *b);
 
 /* ---- Birkhoff-Rott sum without allocation ------------------------------------------------ */
 

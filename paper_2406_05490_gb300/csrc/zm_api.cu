@@ -27,59 +27,85 @@ int cuda_check(cudaError_t e, const char *what)
 
 // ---- profiling ------------------------------------------------------------------------------
 
-static void prof_fold(zm_ctx *c)
+void prof_fold(Prof &pr, cudaStream_t s)
 {
-    if (c->ev_live.empty()) return;
-    cudaStreamSynchronize(c->stream);
-    for (auto &e : c->ev_live) {
+    if (pr.live.empty()) return;
+    cudaStreamSynchronize(s);
+    for (auto &e : pr.live) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) c->prof.ms[e.cls] += ms;
-        c->ev_pool.push_back(e.a);
-        c->ev_pool.push_back(e.b);
+        if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) pr.acc.ms[e.cls] += ms;
+        pr.pool.push_back(e.a);
+        pr.pool.push_back(e.b);
     }
-    c->ev_live.clear();
+    pr.live.clear();
 }
 
-static cudaEvent_t prof_event(zm_ctx *c)
+void prof_release(Prof &pr)
 {
-    if (c->ev_pool.empty()) {
+    for (auto &e : pr.live) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    for (auto e : pr.pool) cudaEventDestroy(e);
+    pr.live.clear();
+    pr.pool.clear();
+}
+
+static cudaEvent_t prof_event(Prof &pr)
+{
+    if (pr.pool.empty()) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
         return e;
     }
-    cudaEvent_t e = c->ev_pool.back();
-    c->ev_pool.pop_back();
+    cudaEvent_t e = pr.pool.back();
+    pr.pool.pop_back();
     return e;
 }
 
-void prof_begin(zm_ctx *c, int cls, cudaEvent_t *a)
+void prof_begin(Prof &pr, cudaStream_t s, int cls, cudaEvent_t *a)
 {
-    c->prof.launches[cls] += 1;
+    pr.acc.launches[cls] += 1;
     *a = nullptr;
-    if (!c->profiling) return;
-    if (c->ev_live.size() >= 4096) prof_fold(c);
-    *a = prof_event(c);
-    if (*a) cudaEventRecord(*a, c->stream);
+    if (!pr.on) return;
+    if (pr.live.size() >= 4096) prof_fold(pr, s);
+    *a = prof_event(pr);
+    if (*a) cudaEventRecord(*a, s);
 }
 
-void prof_end(zm_ctx *c, int cls, cudaEvent_t a)
+void prof_end(Prof &pr, cudaStream_t s, int cls, cudaEvent_t a)
 {
-    if (!c->profiling || !a) return;
-    cudaEvent_t b = prof_event(c);
+    if (!pr.on || !a) return;
+    cudaEvent_t b = prof_event(pr);
     if (!b) return;
-    cudaEventRecord(b, c->stream);
-    c->ev_live.push_back({cls, a, b});
+    cudaEventRecord(b, s);
+    pr.live.push_back({cls, a, b});
 }
+
+// hooks into zm_batch.cu (an FP32C context is a batch of one interface)
+Batch *batch_new_single(const zm_mesh *m, double atwood, double g, double mu, double delta, int *rc);
+void batch_delete(Batch *b);
+const Inst &batch_inst(Batch *b, int k);
+void batch_bind(Batch *b, cudaStream_t s, Prof *p);
+int batch_derivative(Batch *b, int yin);
+int batch_vorticity_rate(Batch *b, int yin);
+int batch_step(Batch *b, double dt, int nsteps);
+int batch_status(Batch *b);
+
+static int stage_index(zm_ctx *c, const double *y) { return y == c->y0 ? 0 : (y == c->ya ? 1 : 2); }
 
 // ---- derivative ---------------------------------------------------------------------------------
 
 // One evaluation of L(y): after it, c->u holds dz/dt and c->phi holds Phi.
 int derivative(zm_ctx *c, const double *y)
 {
+    if (c->batch) {
+        batch_bind(c->batch, c->stream, &c->prof);
+        return batch_derivative(c->batch, stage_index(c, y));
+    }
     int rc = launch_geometry(c, y);
     if (rc) return rc;
     if (c->order == ZM_ORDER_LOW) return launch_riesz(c, y);
-    if (c->fp32c) return launch_br32(c);
     rc = launch_br(c, y);
     if (rc) return rc;
     return launch_reduce(c);
@@ -122,6 +148,10 @@ static int read_status(zm_ctx *c)
         cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
         return set_error(ZM_ERR_TIMEOUT, "a bounded device-side wait gave up (status word set)");
     }
+    if (c->batch) {
+        batch_bind(c->batch, c->stream, &c->prof);
+        return batch_status(c->batch);
+    }
     return ZM_OK;
 }
 
@@ -157,13 +187,14 @@ void zm_destroy(zm_ctx *c)
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    for (auto &e : c->ev_live) {
-        cudaEventDestroy(e.a);
-        cudaEventDestroy(e.b);
+    prof_release(c->prof);
+    if (c->batch) {  // state buffers belong to the batch
+        batch_delete(c->batch);
+        c->batch = nullptr;
+        c->y0 = c->ya = c->yb = c->u = c->phi = c->q = nullptr;
     }
-    for (auto e : c->ev_pool) cudaEventDestroy(e);
     void *bufs[] = {c->y0, c->ya, c->yb, c->u, c->phi, c->q, c->nrm, c->src, c->part,
-                    c->fa, c->fb, c->tw1, c->tw2, c->err, c->flag, c->src_far, c->tinfo};
+                    c->fa, c->fb, c->tw1, c->tw2, c->err, c->flag};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (prev >= 0) cudaSetDevice(prev);
@@ -229,32 +260,38 @@ int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double de
         }
         return true;
     };
-    bool ok = alloc((void **)&c->y0, 5 * N * sizeof(double)) &&
-              alloc((void **)&c->ya, 5 * N * sizeof(double)) &&
-              alloc((void **)&c->yb, 5 * N * sizeof(double)) &&
-              alloc((void **)&c->u, 3 * N * sizeof(double)) &&
-              alloc((void **)&c->phi, N * sizeof(double)) &&
-              alloc((void **)&c->q, N * sizeof(double)) && alloc((void **)&c->err, sizeof(int)) &&
-              alloc((void **)&c->flag, sizeof(int));
-    if (ok && ord == ZM_ORDER_HIGH) {
+    bool ok = alloc((void **)&c->err, sizeof(int)) && alloc((void **)&c->flag, sizeof(int));
+    if (ok && ord == ZM_ORDER_HIGH && fp32c) {
+        int rc = ZM_OK;
+        c->batch = batch_new_single(mesh, atwood, g, mu, delta, &rc);
+        if (!c->batch) {
+            zm_destroy(c);
+            return rc;
+        }
+        const Inst &I = batch_inst(c->batch, 0);
+        c->y0 = I.y[0];
+        c->ya = I.y[1];
+        c->yb = I.y[2];
+        c->u = I.u;
+        c->phi = I.phi;
+        c->q = I.q;
+        c->tiling = I.tiling;
+    } else if (ok) {
+        ok = alloc((void **)&c->y0, 5 * N * sizeof(double)) &&
+             alloc((void **)&c->ya, 5 * N * sizeof(double)) &&
+             alloc((void **)&c->yb, 5 * N * sizeof(double)) &&
+             alloc((void **)&c->u, 3 * N * sizeof(double)) &&
+             alloc((void **)&c->phi, N * sizeof(double)) && alloc((void **)&c->q, N * sizeof(double));
+    }
+    if (ok && ord == ZM_ORDER_HIGH && !fp32c) {
         c->tiling = make_tiling(G);
         const size_t slots = (size_t)c->tiling.ntiles * c->tiling.ts;
-        size_t part_doubles;
-        if (fp32c) {
-            c->plan32 = plan_br32(G, c->tiling, sms);
-            c->src_bytes = slots * kRec32 * sizeof(float);
-            part_doubles = c->plan32.part_doubles;
-            ok = alloc((void **)&c->src_far, slots * kRec32F * sizeof(float)) &&
-                 alloc((void **)&c->tinfo, c->tiling.ntiles * sizeof(float4));
-        } else {
-            c->plan = plan_br(G, c->tiling, sms);
-            c->src_bytes = slots * kRec64 * sizeof(double);
-            part_doubles = (size_t)c->plan.nsplit * 3 * N;
-        }
-        ok = ok && alloc(&c->src, c->src_bytes) && alloc((void **)&c->part, part_doubles * sizeof(double));
+        c->plan = plan_br(G, c->tiling, sms);
+        c->src_bytes = slots * kRec64 * sizeof(double);
+        ok = alloc(&c->src, c->src_bytes) &&
+             alloc((void **)&c->part, (size_t)c->plan.nsplit * 3 * N * sizeof(double));
         // padding slots of edge tiles stay zero for good: zero strength, no contribution
         if (ok) ok = cudaMemset(c->src, 0, c->src_bytes) == cudaSuccess;
-        if (ok && fp32c) ok = init_far_records(c) == ZM_OK;
     }
     if (ok && ord == ZM_ORDER_LOW) ok = alloc((void **)&c->nrm, 3 * N * sizeof(double));
     if (ok) ok = cudaMemset(c->err, 0, sizeof(int)) == cudaSuccess &&
@@ -324,7 +361,10 @@ int zm_velocity(zm_ctx *c, const double *z, const double *w, double *u, double *
     }
     if (!rc) rc = derivative(c, y);
     bool host = false;
-    if (!rc && wdot) {
+    if (!rc && wdot && c->batch) {
+        rc = batch_vorticity_rate(c->batch, stage_index(c, y));  // dw/dt into yb[0, 2N)
+        if (!rc) rc = copy_out(c, wdot, c->yb, 2 * N, &host);
+    } else if (!rc && wdot) {
         if (is_device_ptr(wdot)) {
             rc = launch_vorticity(c, y, wdot, nullptr, nullptr, 0, 0, 0, 0);
         } else {
@@ -343,6 +383,10 @@ int zm_step(zm_ctx *c, double dt, int nsteps)
     if (!std::isfinite(dt) || nsteps < 0)
         return set_error(ZM_ERR_INVALID, "zm_step: dt must be finite and nsteps >= 0");
     // SSP-RK3 (Shu-Osher): stage s writes ca[s] * y0 + cb[s] * (y_s + dt L(y_s))
+    if (c->batch) {
+        batch_bind(c->batch, c->stream, &c->prof);
+        return batch_step(c->batch, dt, nsteps);
+    }
     static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
     static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
     for (int s = 0; s < nsteps; ++s) {
@@ -379,24 +423,24 @@ int zm_set_profiling(zm_ctx *c, int on)
 {
     if (!c) return set_error(ZM_ERR_INVALID, "zm_set_profiling: null context");
     if (on) zm_reset_profile(c);
-    c->profiling = on ? 1 : 0;
+    c->prof.on = on ? 1 : 0;
     return ZM_OK;
 }
 
 int zm_reset_profile(zm_ctx *c)
 {
     if (!c) return set_error(ZM_ERR_INVALID, "zm_reset_profile: null context");
-    prof_fold(c);
-    std::memset(&c->prof, 0, sizeof(c->prof));
+    prof_fold(c->prof, c->stream);
+    std::memset(&c->prof.acc, 0, sizeof(c->prof.acc));
     return ZM_OK;
 }
 
 int zm_get_profile(zm_ctx *c, zm_profile *out)
 {
     if (!c || !out) return set_error(ZM_ERR_INVALID, "zm_get_profile: null argument");
-    prof_fold(c);
+    prof_fold(c->prof, c->stream);
     int rc = cuda_check(cudaStreamSynchronize(c->stream), "zm_get_profile");
-    *out = c->prof;
+    *out = c->prof.acc;
     return rc;
 }
 

@@ -1,0 +1,539 @@
+// zm_batch.cu -- many interfaces of uneven mesh sizes advanced together (high order, FP32C
+// Birkhoff-Rott pair terms).  Each RK3 stage is four launches over the whole batch: the
+// geometry pass, one persistent all-pairs launch over a shared work list (zm_br32.cu), the
+// fixed-point finish (u, Phi) and the vorticity/RK3 pass; a whole step is captured once as a
+// CUDA graph and replayed.  A single FP32C interface (zm_create with ZM_PREC_FP32C) is a batch
+// of one.  Paper counterpart: the ZModel derivative and the TimeIntegrator of Sec. 3.1, per
+// interface; batching many interfaces on one GPU has none.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "zm_stencil.cuh"
+
+namespace zm {
+namespace {
+
+constexpr int kPtb = 256;  // threads per block of the point kernels
+
+__global__ void __launch_bounds__(kPtb)
+    batch_geometry_kernel(const Inst *__restrict__ insts, const int *__restrict__ block_inst, int yin)
+{
+    const Inst &I = insts[block_inst[blockIdx.x]];
+    const int p = (blockIdx.x - I.block0) * kPtb + threadIdx.x;
+    if (p >= I.geom.N) return;
+    const double pref = I.geom.dx1 * I.geom.dx2 / (4.0 * 3.14159265358979323846);
+    geometry_point<kGeoFp32c>(I.geom, I.tiling, p, I.y[yin], pref, I.g, (float)(I.delta * I.delta),
+                              I.near_rec, I.far_rec, I.tinfo, I.gmax, I.q, nullptr);
+}
+
+// u = fixed-point sum * 2^-scale, Phi = q + |u|^2 / 2; clears the accumulators, the tile
+// spheres, max |gamma'| and the work counter for the next evaluation.
+__global__ void __launch_bounds__(kPtb)
+    batch_finish_kernel(const Inst *__restrict__ insts, const int *__restrict__ block_inst,
+                        unsigned long long *counter)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0ull;
+    const Inst &I = insts[block_inst[blockIdx.x]];
+    const int p = (blockIdx.x - I.block0) * kPtb + threadIdx.x;
+    if (p >= I.geom.N) return;
+    const size_t N = I.geom.N;
+    const double inv = ldexp(1.0, -*I.scale);
+    double s[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        s[c] = (double)(long long)I.ufix[c * N + p] * inv;
+        I.ufix[c * N + p] = 0ull;
+        I.u[c * N + p] = s[c];
+    }
+    I.phi[p] = I.q[p] + 0.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    if (p < I.tiling.ntiles) I.tinfo[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (p == 0) *I.gmax = 0u;
+}
+
+// mode 0: dw/dt into the first 2N of stage buffer 2; mode 1: RK3 stage combine into y[yout].
+template <int kMode>
+__global__ void __launch_bounds__(kPtb)
+    batch_vorticity_kernel(const Inst *__restrict__ insts, const int *__restrict__ block_inst, int yin,
+                           int yout, double dt, double ca, double cb)
+{
+    const Inst &I = insts[block_inst[blockIdx.x]];
+    const int p = (blockIdx.x - I.block0) * kPtb + threadIdx.x;
+    if (p >= I.geom.N) return;
+    if (I.mu != 0.0)
+        vorticity_point<true, kMode>(I.geom, p, I.phi, I.y[yin], I.u, I.atwood, I.mu, dt, ca, cb,
+                                     I.y[0], I.y[yout], I.y[2]);
+    else
+        vorticity_point<false, kMode>(I.geom, p, I.phi, I.y[yin], I.u, I.atwood, I.mu, dt, ca, cb,
+                                      I.y[0], I.y[yout], I.y[2]);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+class Batch {
+public:
+    int count = 0;
+    std::vector<Inst> h;
+    Inst *d = nullptr;
+    int *block_inst = nullptr;
+    int nblocks = 0;
+    long long nitems = 0;
+    int ctas = 0, occ = 1, sms = 152;
+    unsigned long long *counter = nullptr;
+    int *err = nullptr;
+    std::vector<void *> slabs;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;  // private stream for graph capture
+    cudaGraphExec_t gexec = nullptr;
+    double gdt = 0.0;
+    Prof own;
+    Prof *prof = &own;
+    int device = 0;
+
+    ~Batch() { release(); }
+
+    void release()
+    {
+        if (stream) cudaStreamSynchronize(stream);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        if (cap) cudaStreamDestroy(cap);
+        cap = nullptr;
+        for (void *s : slabs) cudaFree(s);
+        slabs.clear();
+        if (d) cudaFree(d);
+        if (block_inst) cudaFree(block_inst);
+        if (counter) cudaFree(counter);
+        if (err) cudaFree(err);
+        d = nullptr;
+        block_inst = nullptr;
+        counter = nullptr;
+        err = nullptr;
+        prof_release(own);
+    }
+
+    static int default_chunk(int ntiles) { return std::max(1, std::min(8, ntiles / 16)); }
+
+    int init(int n, const zm_mesh *meshes, const double *atwood, double g, double mu,
+             const double *delta)
+    {
+        count = n;
+        cudaGetDevice(&device);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        occ = br32_occupancy();
+        h.resize(n);
+        long long items = 0;
+        int blocks = 0;
+        for (int k = 0; k < n; ++k) {
+            Inst &I = h[k];
+            std::memset(&I, 0, sizeof(I));
+            const zm_mesh &m = meshes[k];
+            I.geom.n1 = m.n1;
+            I.geom.n2 = m.n2;
+            I.geom.N = m.n1 * m.n2;
+            I.geom.L1 = m.L1;
+            I.geom.L2 = m.L2;
+            I.geom.dx1 = m.L1 / m.n1;
+            I.geom.dx2 = m.L2 / m.n2;
+            I.geom.periodic = m.periodic ? 1 : 0;
+            I.tiling = make_tiling(I.geom);
+            I.atwood = atwood[k];
+            I.g = g;
+            I.mu = mu;
+            I.delta = delta[k];
+            I.block0 = blocks;
+            blocks += (I.geom.N + kPtb - 1) / kPtb;
+            I.chunk = default_chunk(I.tiling.ntiles);
+            I.nchunks = (I.tiling.ntiles + I.chunk - 1) / I.chunk;
+            I.item0 = items;
+            items += (long long)I.tiling.ntiles * I.nchunks;
+            // one slab per interface
+            const size_t N = I.geom.N, slots = (size_t)I.tiling.ntiles * I.tiling.ts;
+            size_t off[12], total = 0;
+            const size_t sz[12] = {5 * N * 8, 5 * N * 8, 5 * N * 8, 3 * N * 8, N * 8, N * 8, 3 * N * 8,
+                                   slots * kRec32 * 4, slots * kRec32F * 4,
+                                   (size_t)I.tiling.ntiles * 16, 4, 4};
+            for (int s = 0; s < 12; ++s) {
+                off[s] = total;
+                total += align256(sz[s]);
+            }
+            void *slab = nullptr;
+            if (cudaMalloc(&slab, total) != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(ZM_ERR_NOMEM, "batch: device allocation failed");
+            }
+            slabs.push_back(slab);
+            char *b = static_cast<char *>(slab);
+            if (cudaMemset(slab, 0, total) != cudaSuccess)
+                return set_error(ZM_ERR_CUDA, "batch: memset failed");
+            for (int s = 0; s < 3; ++s) I.y[s] = reinterpret_cast<double *>(b + off[s]);
+            I.u = reinterpret_cast<double *>(b + off[3]);
+            I.phi = reinterpret_cast<double *>(b + off[4]);
+            I.q = reinterpret_cast<double *>(b + off[5]);
+            I.ufix = reinterpret_cast<unsigned long long *>(b + off[6]);
+            I.near_rec = reinterpret_cast<float *>(b + off[7]);
+            I.far_rec = reinterpret_cast<float *>(b + off[8]);
+            I.tinfo = reinterpret_cast<float4 *>(b + off[9]);
+            I.gmax = reinterpret_cast<unsigned int *>(b + off[10]);
+            I.scale = reinterpret_cast<int *>(b + off[11]);
+            init_far_records(I.far_rec, I.tiling.ntiles, (float)(I.delta * I.delta), nullptr);
+        }
+        nblocks = blocks;
+        nitems = items;
+        ctas = (int)std::min<long long>(nitems, (long long)occ * sms);
+        std::vector<int> bi(nblocks);
+        for (int k = 0; k < n; ++k) {
+            const int nb = (h[k].geom.N + kPtb - 1) / kPtb;
+            for (int q = 0; q < nb; ++q) bi[h[k].block0 + q] = k;
+        }
+        if (cudaMalloc(&d, n * sizeof(Inst)) != cudaSuccess ||
+            cudaMalloc(&block_inst, nblocks * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&counter, sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ZM_ERR_NOMEM, "batch: device allocation failed");
+        }
+        cudaMemcpy(block_inst, bi.data(), nblocks * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemset(counter, 0, sizeof(unsigned long long));
+        cudaMemset(err, 0, sizeof(int));
+        int rc = upload();
+        if (rc) return rc;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+            return set_error(ZM_ERR_CUDA, "batch: stream creation failed");
+        return cuda_check(cudaDeviceSynchronize(), "batch init");
+    }
+
+    int upload()
+    {
+        return cuda_check(cudaMemcpy(d, h.data(), count * sizeof(Inst), cudaMemcpyHostToDevice),
+                          "batch descriptor upload");
+    }
+
+    // Work-item size (source tiles per item) for every interface; invalidates the step graph.
+    int set_chunk(int chunk)
+    {
+        long long items = 0;
+        for (auto &I : h) {
+            I.chunk = chunk > 0 ? std::min(chunk, I.tiling.ntiles) : default_chunk(I.tiling.ntiles);
+            I.nchunks = (I.tiling.ntiles + I.chunk - 1) / I.chunk;
+            I.item0 = items;
+            items += (long long)I.tiling.ntiles * I.nchunks;
+        }
+        nitems = items;
+        ctas = (int)std::min<long long>(nitems, (long long)occ * sms);
+        drop_graph();
+        cudaStreamSynchronize(stream);
+        return upload();
+    }
+
+    void drop_graph()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+    }
+
+    // One evaluation of L on y[yin] of every interface: u and Phi of each interface.
+    int derivative(int yin, cudaStream_t s)
+    {
+        cudaEvent_t ev = nullptr;
+        prof_begin(*prof, s, ZM_K_GEOMETRY, &ev);
+        batch_geometry_kernel<<<nblocks, kPtb, 0, s>>>(d, block_inst, yin);
+        prof_end(*prof, s, ZM_K_GEOMETRY, ev);
+        int rc = cuda_check(cudaGetLastError(), "batch geometry launch");
+        if (rc) return rc;
+        prof_begin(*prof, s, ZM_K_BR, &ev);
+        rc = launch_br32_batch(d, count, nitems, ctas, counter, err, s);
+        prof_end(*prof, s, ZM_K_BR, ev);
+        for (auto &I : h) prof->acc.pairs += (int64_t)I.geom.N * I.geom.N;
+        if (rc) return rc;
+        prof_begin(*prof, s, ZM_K_REDUCE, &ev);
+        batch_finish_kernel<<<nblocks, kPtb, 0, s>>>(d, block_inst, counter);
+        prof_end(*prof, s, ZM_K_REDUCE, ev);
+        return cuda_check(cudaGetLastError(), "batch finish launch");
+    }
+
+    int vorticity(int yin, int mode, double dt, double ca, double cb, int yout, cudaStream_t s)
+    {
+        cudaEvent_t ev = nullptr;
+        prof_begin(*prof, s, ZM_K_VORT, &ev);
+        if (mode == 0)
+            batch_vorticity_kernel<0><<<nblocks, kPtb, 0, s>>>(d, block_inst, yin, yout, dt, ca, cb);
+        else
+            batch_vorticity_kernel<1><<<nblocks, kPtb, 0, s>>>(d, block_inst, yin, yout, dt, ca, cb);
+        prof_end(*prof, s, ZM_K_VORT, ev);
+        return cuda_check(cudaGetLastError(), "batch vorticity launch");
+    }
+
+    // SSP-RK3 (Shu-Osher): stage st writes ca y0 + cb (y_st + dt L(y_st)).
+    int rk3_step_launches(double dt, cudaStream_t s)
+    {
+        static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+        static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+        static const int yin[3] = {0, 1, 2}, yout[3] = {1, 2, 0};
+        for (int st = 0; st < 3; ++st) {
+            int rc = derivative(yin[st], s);
+            if (!rc) rc = vorticity(yin[st], 1, dt, ca[st], cb[st], yout[st], s);
+            if (rc) return rc;
+        }
+        return ZM_OK;
+    }
+
+    int step(double dt, int nsteps)
+    {
+        if (nsteps <= 0) return ZM_OK;
+        if (prof->on) {  // event timing needs plain launches
+            for (int k = 0; k < nsteps; ++k) {
+                int rc = rk3_step_launches(dt, stream);
+                if (rc) return rc;
+            }
+            return ZM_OK;
+        }
+        if (!gexec || gdt != dt) {
+            drop_graph();
+            cudaGraph_t graph = nullptr;
+            int rc = cuda_check(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal),
+                                "step graph capture");
+            if (rc) return rc;
+            rc = rk3_step_launches(dt, cap);
+            cudaError_t e = cudaStreamEndCapture(cap, &graph);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            rc = cuda_check(e, "step graph capture end");
+            if (!rc) rc = cuda_check(cudaGraphInstantiate(&gexec, graph, 0), "step graph instantiate");
+            if (graph) cudaGraphDestroy(graph);
+            if (rc) return rc;
+            gdt = dt;
+        }
+        for (int k = 0; k < nsteps; ++k) {
+            int rc = cuda_check(cudaGraphLaunch(gexec, stream), "step graph launch");
+            if (rc) return rc;
+        }
+        // launches inside the graph, for the launch counters (4 per stage)
+        prof->acc.launches[ZM_K_GEOMETRY] += 3LL * nsteps;
+        prof->acc.launches[ZM_K_BR] += 3LL * nsteps;
+        prof->acc.launches[ZM_K_REDUCE] += 3LL * nsteps;
+        prof->acc.launches[ZM_K_VORT] += 3LL * nsteps;
+        for (auto &I : h) prof->acc.pairs += 3LL * nsteps * (int64_t)I.geom.N * I.geom.N;
+        return ZM_OK;
+    }
+
+    int status()
+    {
+        int hs = 0;
+        int rc = cuda_check(cudaMemcpyAsync(&hs, err, sizeof(int), cudaMemcpyDeviceToHost, stream),
+                            "batch status read");
+        if (!rc) rc = cuda_check(cudaStreamSynchronize(stream), "batch synchronize");
+        if (!rc && (hs & kErrTimeout)) {
+            cudaMemsetAsync(err, 0, sizeof(int), stream);
+            rc = set_error(ZM_ERR_TIMEOUT, "a bounded device-side wait gave up (status word set)");
+        }
+        return rc;
+    }
+};
+
+// ---- hooks used by zm_api.cu for an FP32C context (a batch of one) ---------------------------
+
+Batch *batch_new_single(const zm_mesh *m, double atwood, double g, double mu, double delta, int *rc)
+{
+    Batch *b = new (std::nothrow) Batch();
+    if (!b) {
+        *rc = set_error(ZM_ERR_NOMEM, "batch: host allocation failed");
+        return nullptr;
+    }
+    *rc = b->init(1, m, &atwood, g, mu, &delta);
+    if (*rc) {
+        delete b;
+        return nullptr;
+    }
+    return b;
+}
+void batch_delete(Batch *b) { delete b; }
+const Inst &batch_inst(Batch *b, int k) { return b->h[k]; }
+void batch_bind(Batch *b, cudaStream_t s, Prof *p)
+{
+    if (b->stream != s) b->drop_graph();
+    b->stream = s;
+    b->prof = p;
+}
+int batch_derivative(Batch *b, int yin) { return b->derivative(yin, b->stream); }
+int batch_vorticity_rate(Batch *b, int yin) { return b->vorticity(yin, 0, 0, 0, 0, 0, b->stream); }
+int batch_step(Batch *b, double dt, int nsteps) { return b->step(dt, nsteps); }
+int batch_status(Batch *b) { return b->status(); }
+
+}  // namespace zm
+
+// ---- C ABI -------------------------------------------------------------------------------------
+
+using namespace zm;
+
+struct zm_batch {
+    Batch b;
+};
+
+static bool batch_index_ok(zm_batch *bt, int32_t index)
+{
+    return bt && index >= 0 && index < bt->b.count;
+}
+
+static bool dev_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int batch_copy(zm_batch *bt, void *dst, const void *src, size_t bytes, bool *host)
+{
+    const bool sd = dev_ptr(src), dd = dev_ptr(dst);
+    if (!sd || !dd) *host = true;
+    return cuda_check(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, bt->b.stream), "batch copy");
+}
+
+extern "C" {
+
+int zm_batch_create(int32_t count, const zm_mesh *meshes, const double *atwood, double g, double mu,
+                    const double *delta, zm_batch **out)
+{
+    if (!out || !meshes || !atwood || !delta || count < 1 || count > (1 << 16))
+        return set_error(ZM_ERR_INVALID, "zm_batch_create: bad arguments");
+    *out = nullptr;
+    if (!std::isfinite(g) || !(mu >= 0) || !std::isfinite(mu))
+        return set_error(ZM_ERR_INVALID, "zm_batch_create: g must be finite and mu >= 0");
+    for (int k = 0; k < count; ++k) {
+        const zm_mesh &m = meshes[k];
+        if (m.n1 < 5 || m.n2 < 5 || (int64_t)m.n1 * m.n2 > (1 << 24) || !(m.L1 > 0) || !(m.L2 > 0) ||
+            !std::isfinite(m.L1) || !std::isfinite(m.L2) || !std::isfinite(atwood[k]) ||
+            !(delta[k] > 0) || !std::isfinite(delta[k]))
+            return set_error(ZM_ERR_INVALID, "zm_batch_create: bad mesh or parameter at index " +
+                                                 std::to_string(k));
+    }
+    zm_batch *bt = new (std::nothrow) zm_batch();
+    if (!bt) return set_error(ZM_ERR_NOMEM, "zm_batch_create: host allocation failed");
+    int rc = bt->b.init(count, meshes, atwood, g, mu, delta);
+    if (rc) {
+        delete bt;
+        return rc;
+    }
+    *out = bt;
+    return ZM_OK;
+}
+
+int zm_batch_set_stream(zm_batch *bt, void *stream)
+{
+    if (!bt) return set_error(ZM_ERR_INVALID, "zm_batch_set_stream: null batch");
+    batch_bind(&bt->b, static_cast<cudaStream_t>(stream), bt->b.prof);
+    return ZM_OK;
+}
+
+int zm_batch_set_state(zm_batch *bt, int32_t index, const double *z, const double *w)
+{
+    if (!batch_index_ok(bt, index) || !z || !w)
+        return set_error(ZM_ERR_INVALID, "zm_batch_set_state: bad arguments");
+    const Inst &I = bt->b.h[index];
+    const size_t N = I.geom.N;
+    bool host = false;
+    int rc = batch_copy(bt, I.y[0], z, 3 * N * sizeof(double), &host);
+    if (!rc) rc = batch_copy(bt, I.y[0] + 3 * N, w, 2 * N * sizeof(double), &host);
+    if (!rc && host) rc = cuda_check(cudaStreamSynchronize(bt->b.stream), "zm_batch_set_state");
+    return rc;
+}
+
+int zm_batch_get_state(zm_batch *bt, int32_t index, double *z, double *w)
+{
+    if (!batch_index_ok(bt, index)) return set_error(ZM_ERR_INVALID, "zm_batch_get_state: bad arguments");
+    const Inst &I = bt->b.h[index];
+    const size_t N = I.geom.N;
+    bool host = false;
+    int rc = ZM_OK;
+    if (z) rc = batch_copy(bt, z, I.y[0], 3 * N * sizeof(double), &host);
+    if (!rc && w) rc = batch_copy(bt, w, I.y[0] + 3 * N, 2 * N * sizeof(double), &host);
+    if (!rc && host) rc = bt->b.status();
+    return rc;
+}
+
+int zm_batch_velocity(zm_batch *bt)
+{
+    if (!bt) return set_error(ZM_ERR_INVALID, "zm_batch_velocity: null batch");
+    int rc = bt->b.derivative(0, bt->b.stream);
+    if (!rc) rc = bt->b.vorticity(0, 0, 0, 0, 0, 0, bt->b.stream);
+    return rc;
+}
+
+int zm_batch_get_velocity(zm_batch *bt, int32_t index, double *u, double *wdot)
+{
+    if (!batch_index_ok(bt, index)) return set_error(ZM_ERR_INVALID, "zm_batch_get_velocity: bad arguments");
+    const Inst &I = bt->b.h[index];
+    const size_t N = I.geom.N;
+    bool host = false;
+    int rc = ZM_OK;
+    if (u) rc = batch_copy(bt, u, I.u, 3 * N * sizeof(double), &host);
+    if (!rc && wdot) rc = batch_copy(bt, wdot, I.y[2], 2 * N * sizeof(double), &host);
+    if (!rc && host) rc = bt->b.status();
+    return rc;
+}
+
+int zm_batch_step(zm_batch *bt, double dt, int32_t nsteps)
+{
+    if (!bt || !std::isfinite(dt) || nsteps < 0) return set_error(ZM_ERR_INVALID, "zm_batch_step: bad arguments");
+    return bt->b.step(dt, nsteps);
+}
+
+int zm_batch_sync(zm_batch *bt)
+{
+    if (!bt) return set_error(ZM_ERR_INVALID, "zm_batch_sync: null batch");
+    return bt->b.status();
+}
+
+int zm_batch_set_chunk(zm_batch *bt, int32_t chunk)
+{
+    if (!bt || chunk < 0) return set_error(ZM_ERR_INVALID, "zm_batch_set_chunk: bad arguments");
+    return bt->b.set_chunk(chunk);
+}
+
+int zm_batch_info(zm_batch *bt, int64_t *points, int64_t *pairs_per_eval, int64_t *work_items,
+                  int32_t *ctas)
+{
+    if (!bt) return set_error(ZM_ERR_INVALID, "zm_batch_info: null batch");
+    int64_t pts = 0, prs = 0;
+    for (auto &I : bt->b.h) {
+        pts += I.geom.N;
+        prs += (int64_t)I.geom.N * I.geom.N;
+    }
+    if (points) *points = pts;
+    if (pairs_per_eval) *pairs_per_eval = prs;
+    if (work_items) *work_items = bt->b.nitems;
+    if (ctas) *ctas = bt->b.ctas;
+    return ZM_OK;
+}
+
+int zm_batch_set_profiling(zm_batch *bt, int on)
+{
+    if (!bt) return set_error(ZM_ERR_INVALID, "zm_batch_set_profiling: null batch");
+    prof_fold(*bt->b.prof, bt->b.stream);
+    std::memset(&bt->b.prof->acc, 0, sizeof(zm_profile));
+    bt->b.prof->on = on ? 1 : 0;
+    return ZM_OK;
+}
+
+int zm_batch_get_profile(zm_batch *bt, zm_profile *out)
+{
+    if (!bt || !out) return set_error(ZM_ERR_INVALID, "zm_batch_get_profile: null argument");
+    prof_fold(*bt->b.prof, bt->b.stream);
+    int rc = cuda_check(cudaStreamSynchronize(bt->b.stream), "zm_batch_get_profile");
+    *out = bt->b.prof->acc;
+    return rc;
+}
+
+void zm_batch_destroy(zm_batch *bt) { delete bt; }
+
+}  // extern "C"

@@ -158,7 +158,7 @@ int launch_br(zm_ctx *c, const double *y)
         g.N, y, static_cast<const double *>(c->src), c->tiling.ntiles, p.tiles_per_split,
         c->delta * c->delta, c->part, c->err);
     prof_end(c, ZM_K_BR, ev);
-    c->prof.pairs += (int64_t)g.N * (int64_t)g.N;
+    c->prof.acc.pairs += (int64_t)g.N * (int64_t)g.N;
     return cuda_check(cudaGetLastError(), "Birkhoff-Rott kernel launch");
 }
 

@@ -1,26 +1,31 @@
-// zm_br32.cu -- FP32-compensated all-pairs Birkhoff-Rott sum (paper Sec. 2 BRSolver, Sec. 3.2.1
-// ExactBRSolver, the high-order model), with FP64 accumulation across source tiles:
-//     u_i = sum_j (z_j - z_i) x gamma'_j / (|z_j - z_i|^2 + delta^2)^(3/2).
+// zm_br32.cu -- FP32-compensated all-pairs Birkhoff-Rott sum over a batch of interfaces (paper
+// Sec. 2 BRSolver, Sec. 3.2.1 ExactBRSolver, the high-order model):
+//     u_i = sum_j (z_j - z_i) x gamma'_j / (|z_j - z_i|^2 + delta^2)^(3/2),   i, j in one interface.
 //
-// Work decomposition.  Targets come in groups of one 16 x 16 mesh tile (256 targets, 64
-// threads x 4 targets in registers); sources in 16 x 16 tiles.  The iteration space
-// (target group x source tile) is cut into equal contiguous ranges, one per persistent CTA
-// (a stream-K decomposition): every CTA does the same number of tile pairs, whatever the mesh
-// size, and writes one partial sum per target group its range touches.  A second kernel adds
-// the partials of each target in a fixed order and forms Phi, so results are deterministic.
+// Work.  A work item is (interface, target tile, chunk of consecutive source tiles); tiles are
+// 16 x 16 mesh patches (256 points).  Persistent CTAs of 64 threads (4 targets per thread, one
+// target tile per CTA at a time) take items from a global atomic counter, so near and far tile
+// pairs of unequal cost and interfaces of unequal size balance dynamically.  Source tiles
+// arrive by 1D bulk TMA (cp.async.bulk) into a double-buffered shared-memory stage; thread 0
+// runs ahead one tile, choosing each tile's path and copying the matching record.
 //
-// Two source paths, chosen per (target group, source tile) from bounding spheres:
-//   near (spheres within 1.25 x the sum of radii): positions as FP32 hi/lo pairs,
-//     r = (zh_j - zh_i) + (zl_j - zl_i), then the direct formula -- 23 FP32 + 1 MUFU per pair;
-//   far: tile-local coordinates s_j = z_j - c_T and t_i = z_i - c_T (c_T the tile centre), the
-//     distance in Gram form |r|^2 + delta^2 = (|s_j|^2 + delta^2) + |t_i|^2 - 2 s_j . t_i, and the
-//     cross product split as sum K (s_j x gamma_j) - t_i x sum K gamma_j -- 12 FP32 + 1 MUFU per
-//     pair.  With the spheres apart, |s|, |t| and |r| are of one order, so neither the Gram
-//     form nor the split loses more than a few units of FP32 rounding.  Two adjacent sources
-//     share one packed FP32x2 instruction (fma/mul/add .f32x2): the FP32 work is unchanged but
-//     issue slots halve, so the loop is bound by the FP32 pipe rather than by issue.
-// Source tiles of both kinds arrive by 1D bulk TMA (cp.async.bulk) into a double-buffered
-// shared-memory stage; every thread reads the same source at once (broadcast).
+// Two source paths, per (target tile, source tile), from bounding spheres:
+//   near (centres closer than 1.25 x the sum of radii): positions as FP32 hi/lo pairs,
+//     r = (zh_j - zh_i) + (zl_j - zl_i), the direct formula -- 23 FP32 + 1 MUFU per pair;
+//   far: tile-local coordinates s_j = z_j - c_T and t_i = z_i - c_T (c_T the source tile's
+//     centre), |r|^2 + delta^2 in Gram form (|s_j|^2 + delta^2) + |t_i|^2 - 2 s_j . t_i and the
+//     cross product split as sum K (s_j x gamma_j) - t_i x sum K gamma_j: 12 FP32 + 1 MUFU per
+//     pair.  With the spheres apart, |s|, |t| and |r| are of one order, so neither form loses
+//     more than a few units of FP32 rounding.  Two adjacent sources share one packed FP32x2
+//     instruction (fma/mul/add .f32x2), which halves issue slots for the same FP32 work.
+//
+// Accumulation.  Each (target, source tile) partial is an FP32 sum over 256 sources.  Partials
+// are added exactly in 64-bit fixed point, value * 2^S with S per interface chosen from the
+// bound |u| <= N max|gamma'| (2 / (3 sqrt 3)) / delta^2 so that no sum can overflow.  Integer
+// addition is associative: the result is bitwise the same whatever the scheduling or the
+// other interfaces in the batch, and it carries more than FP64's precision across tiles.
+// Partials collect in shared memory while a CTA stays on one target tile and reach the
+// per-interface accumulators by integer atomics when it moves on.
 #include <algorithm>
 
 #include "zm_internal.cuh"
@@ -28,10 +33,9 @@
 namespace zm {
 namespace {
 
-constexpr int kT = 64;     // threads per CTA
-constexpr int kR = 4;      // targets per thread
-constexpr int kTs = 256;   // sources per tile (16 x 16)
-constexpr int kGroup = 1;  // tiles per target group
+constexpr int kT = 64;    // threads per CTA
+constexpr int kR = 4;     // targets per thread: one 16 x 16 target tile per CTA
+constexpr int kTs = 256;  // sources per tile
 constexpr float kFarFactor = 1.25f;
 
 typedef unsigned long long u64;  // two packed floats (low word first)
@@ -73,133 +77,148 @@ __device__ __forceinline__ u64 rsqrt2(u64 v)
     return pack2(dev::rsqrt_approx(lo), dev::rsqrt_approx(hi));
 }
 
-struct Args {
-    int n1, n2, N;
-    int nt2, ntiles, ng2, ngroups;
-    long long units;
-    int ctas, kseg;
-    float d2;
-    const float *near_rec;  // [tile][9][256]: zh, zl, gamma'
-    const float *far_rec;   // [tile][10][256]: s, |s|^2 + delta^2, gamma', s x gamma'
-    const float4 *tinfo;    // [tile]: centre (x, y, z), radius
-    double *part;           // [ctas * kseg][3][512]
-    int *err;
+// Fixed-point scale of one interface: |sum| <= N max|gamma'| * 0.385 / delta^2 < 2^(e+1); keep
+// the scaled sum below 2^61.
+__device__ __forceinline__ int fix_scale(const Inst &I)
+{
+    const float gm = __uint_as_float(*I.gmax);
+    const double bound = (double)gm * (double)I.geom.N * 0.385 / (I.delta * I.delta) + 1e-300;
+    return max(0, min(100, 60 - ilogb(bound)));
+}
+
+struct Unit {
+    int inst;  // -1: no more work
+    int tile;  // target tile
+    int src;   // source tile
+    int far;
 };
 
-__device__ __forceinline__ int cta_of_unit(long long k, long long units, int ctas)
-{
-    return (int)(((k + 1) * ctas - 1) / units);
-}
-
-// bounding sphere of target group G (one or two tiles)
-__device__ __forceinline__ void group_sphere(const Args &a, int G, float3 &c, float &rad)
-{
-    const int ti = G / a.ng2, gj = G - ti * a.ng2;
-    const int t0 = ti * a.nt2 + kGroup * gj;
-    const float4 s0 = a.tinfo[t0];
-    if (kGroup > 1 && kGroup * gj + 1 < a.nt2) {
-        const float4 s1 = a.tinfo[t0 + 1];
-        c = make_float3(0.5f * (s0.x + s1.x), 0.5f * (s0.y + s1.y), 0.5f * (s0.z + s1.z));
-        const float d0 = sqrtf((s0.x - c.x) * (s0.x - c.x) + (s0.y - c.y) * (s0.y - c.y) + (s0.z - c.z) * (s0.z - c.z));
-        const float d1 = sqrtf((s1.x - c.x) * (s1.x - c.x) + (s1.y - c.y) * (s1.y - c.y) + (s1.z - c.z) * (s1.z - c.z));
-        rad = fmaxf(d0 + s0.w, d1 + s1.w);
-    } else {
-        c = make_float3(s0.x, s0.y, s0.z);
-        rad = s0.w;
-    }
-}
-
-__device__ __forceinline__ bool is_far(const Args &a, int G, int S)
-{
-    float3 c;
-    float rg;
-    group_sphere(a, G, c, rg);
-    const float4 t = a.tinfo[S];
-    const float dx = c.x - t.x, dy = c.y - t.y, dz = c.z - t.z;
-    return sqrtf(dx * dx + dy * dy + dz * dz) >= kFarFactor * (rg + t.w);
-}
-
-// thread 0: decide the path of unit k (flag kept in shared memory for the consumers) and start
-// the bulk copy of its source tile into stage `buf`
-__device__ __forceinline__ void issue_unit(const Args &a, long long u, float *stage, int *flag,
-                                           uint64_t *bar)
-{
-    const int G = (int)(u / a.ntiles), S = (int)(u - (long long)G * a.ntiles);
-    const bool far = is_far(a, G, S);
-    *flag = far ? 1 : 0;
-    if (far)
-        dev::tma_load_1d(stage, a.far_rec + (size_t)S * kRec32F * kTs, kRec32F * kTs * sizeof(float), bar);
-    else
-        dev::tma_load_1d(stage, a.near_rec + (size_t)S * kRec32 * kTs, kRec32 * kTs * sizeof(float), bar);
-}
-
-__global__ void __launch_bounds__(kT, 8) br32_kernel(Args a)
+__global__ void __launch_bounds__(kT, 8)
+    br32_batch_kernel(const Inst *__restrict__ insts, int ninst, long long nitems,
+                      unsigned long long *counter, int *err)
 {
     __shared__ __align__(128) float stage[2][kRec32F * kTs];
-    // FP64 accumulators of this thread's targets, [component][target r][thread]
-    __shared__ double acc[3][kR][kT];
+    __shared__ long long acc[3][kR][kT];  // fixed-point partial sums of this thread's targets
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int flag[2];
+    __shared__ Unit unit[2];
 
     const int tid = threadIdx.x;
-    const int cta = blockIdx.x;
-    const long long u0 = (long long)cta * a.units / a.ctas;
-    const long long u1 = (long long)(cta + 1) * a.units / a.ctas;
-    const int nu = (int)(u1 - u0);
-    const int g_first = (int)(u0 / a.ntiles);
+
+    // ---- producer state (thread 0) ----
+    int p_inst = 0, p_tile = 0, p_next = 0, p_left = 0;
+    bool p_done = false;
+    auto produce = [&](int buf) {
+        while (p_left == 0 && !p_done) {
+            const long long it = (long long)atomicAdd(counter, 1ull);
+            if (it >= nitems) {
+                p_done = true;
+                break;
+            }
+            int lo = 0, hi = ninst - 1;  // last interface with item0 <= it
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (insts[mid].item0 <= it) lo = mid;
+                else hi = mid - 1;
+            }
+            const Inst &I = insts[lo];
+            const long long local = it - I.item0;
+            p_inst = lo;
+            p_tile = (int)(local / I.nchunks);
+            const int ch = (int)(local - (long long)p_tile * I.nchunks);
+            p_next = ch * I.chunk;
+            p_left = min(I.chunk, I.tiling.ntiles - p_next);
+        }
+        if (p_done) {
+            unit[buf].inst = -1;
+            return;
+        }
+        const Inst &I = insts[p_inst];
+        const int S = p_next++;
+        --p_left;
+        const float4 a = I.tinfo[p_tile], b = I.tinfo[S];
+        const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+        const bool far = sqrtf(dx * dx + dy * dy + dz * dz) >= kFarFactor * (a.w + b.w);
+        unit[buf].inst = p_inst;
+        unit[buf].tile = p_tile;
+        unit[buf].src = S;
+        unit[buf].far = far ? 1 : 0;
+        if (far)
+            dev::tma_load_1d(stage[buf], I.far_rec + (size_t)S * kRec32F * kTs,
+                             kRec32F * kTs * sizeof(float), &bar[buf]);
+        else
+            dev::tma_load_1d(stage[buf], I.near_rec + (size_t)S * kRec32 * kTs,
+                             kRec32 * kTs * sizeof(float), &bar[buf]);
+    };
 
     if (tid == 0) {
         dev::mbar_init(&bar[0], 1);
         dev::mbar_init(&bar[1], 1);
         dev::fence_mbar_init();
     }
+#pragma unroll
+    for (int r = 0; r < kR; ++r) acc[0][r][tid] = acc[1][r][tid] = acc[2][r][tid] = 0;
     __syncthreads();
     if (tid == 0) {
-        for (int k = 0; k < 2 && k < nu; ++k) issue_unit(a, u0 + k, stage[k], &flag[k], &bar[k]);
+        produce(0);
+        produce(1);
     }
     __syncthreads();
 
-#pragma unroll
-    for (int r = 0; r < kR; ++r) acc[0][r][tid] = acc[1][r][tid] = acc[2][r][tid] = 0.0;
-    int cur_g = -1;
-    int t_of[2];  // tiles of the current group (the second repeats the first for kGroup = 1)
-    t_of[0] = t_of[1] = 0;
-    int bad = 0, kb = 0;
+    // ---- consumer state (all threads) ----
+    int c_inst = -1, c_tile = -1;
+    float c_d2 = 0.0f, c_mult = 1.0f;
+    const float *c_near = nullptr;
 
-    for (int k = 0; k < nu; ++k) {
-        const long long u = u0 + k;
-        const int G = (int)(u / a.ntiles), S = (int)(u - (long long)G * a.ntiles);
-        if (G != cur_g) {
-            if (cur_g >= 0) {
-                double *o = a.part + (size_t)(cta * a.kseg + (cur_g - g_first)) * 3 * (kGroup * kTs);
+    auto flush = [&]() {
+        if (c_inst < 0) return;
+        const Inst &I = insts[c_inst];
+        const int ti = c_tile / I.tiling.nt2, tj = c_tile - ti * I.tiling.nt2;
+        const size_t N = I.geom.N;
 #pragma unroll
-                for (int r = 0; r < kR; ++r) {
-                    const int idx = (r / (kR / kGroup)) * kTs + (r % (kR / kGroup)) * kT + tid;
+        for (int r = 0; r < kR; ++r) {
+            const int slot = r * kT + tid;
+            const int i = ti * 16 + (slot >> 4), j = tj * 16 + (slot & 15);
+            if (i < I.geom.n1 && j < I.geom.n2) {
+                const size_t p = (size_t)i * I.geom.n2 + j;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        o[c * (kGroup * kTs) + idx] = acc[c][r][tid];
-                        acc[c][r][tid] = 0.0;
-                    }
+                for (int c = 0; c < 3; ++c) {
+                    const long long v = acc[c][r][tid];
+                    if (v) atomicAdd(&I.ufix[c * N + p], (unsigned long long)v);
                 }
             }
-            cur_g = G;
-            const int ti = G / a.ng2, gj = G - ti * a.ng2;
-            t_of[0] = ti * a.nt2 + kGroup * gj;
-            t_of[1] = (kGroup > 1 && kGroup * gj + 1 < a.nt2) ? t_of[0] + 1 : t_of[0];
+            acc[0][r][tid] = acc[1][r][tid] = acc[2][r][tid] = 0;
         }
+    };
+
+    int bad = 0, kb = 0;
+    for (int k = 0;; ++k) {
         const int b = k & 1;
+        const Unit un = unit[b];
+        if (un.inst < 0) break;
         const bool ok = dev::mbar_wait_bounded(&bar[b], (k >> 1) & 1);
+        if (un.inst != c_inst || un.tile != c_tile) {
+            flush();
+            if (un.inst != c_inst) {
+                const Inst &I = insts[un.inst];
+                const int sc = fix_scale(I);
+                c_mult = __int_as_float((127 + sc) << 23);  // 2^scale, exact
+                c_d2 = (float)(I.delta * I.delta);
+                c_near = I.near_rec;
+                if (tid == 0) *I.scale = sc;
+            }
+            c_inst = un.inst;
+            c_tile = un.tile;
+        }
         if (ok) {
             const float *s = stage[b];
-            if (flag[b]) {
+            if (un.far) {
                 // ---- far path ------------------------------------------------------------
-                const float4 cs = a.tinfo[S];
+                const float4 cs = insts[c_inst].tinfo[un.src];
                 u64 m2x[kR], m2y[kR], m2z[kR], bb[kR];
                 u64 ax[kR], ay[kR], az[kR], gxs[kR], gys[kR], gzs[kR];
 #pragma unroll
                 for (int r = 0; r < kR; ++r) {
-                    const float *tr = a.near_rec + (size_t)t_of[r / (kR / kGroup)] * kRec32 * kTs +
-                                      (r % (kR / kGroup)) * kT + tid;
+                    const float *tr = c_near + (size_t)c_tile * kRec32 * kTs + r * kT + tid;
                     const float tx = (__ldg(tr) - cs.x) + __ldg(tr + 3 * kTs);
                     const float ty = (__ldg(tr + kTs) - cs.y) + __ldg(tr + 4 * kTs);
                     const float tz = (__ldg(tr + 2 * kTs) - cs.z) + __ldg(tr + 5 * kTs);
@@ -234,17 +253,19 @@ __global__ void __launch_bounds__(kT, 8) br32_kernel(Args a)
                     // t = -m2 / 2 exactly (both lanes of m2 hold -2 t)
                     const float tx = -0.25f * sum2(m2x[r]), ty = -0.25f * sum2(m2y[r]), tz = -0.25f * sum2(m2z[r]);
                     const float bx = sum2(gxs[r]), by = sum2(gys[r]), bz = sum2(gzs[r]);
-                    acc[0][r][tid] += (double)(sum2(ax[r]) - fmaf(ty, bz, -tz * by));
-                    acc[1][r][tid] += (double)(sum2(ay[r]) - fmaf(tz, bx, -tx * bz));
-                    acc[2][r][tid] += (double)(sum2(az[r]) - fmaf(tx, by, -ty * bx));
+                    const float vx = sum2(ax[r]) - fmaf(ty, bz, -tz * by);
+                    const float vy = sum2(ay[r]) - fmaf(tz, bx, -tx * bz);
+                    const float vz = sum2(az[r]) - fmaf(tx, by, -ty * bx);
+                    acc[0][r][tid] += __float2ll_rn(vx * c_mult);
+                    acc[1][r][tid] += __float2ll_rn(vy * c_mult);
+                    acc[2][r][tid] += __float2ll_rn(vz * c_mult);
                 }
             } else {
                 // ---- near path -----------------------------------------------------------
                 float hx[kR], hy[kR], hz[kR], lx[kR], ly[kR], lz[kR], px[kR], py[kR], pz[kR];
 #pragma unroll
                 for (int r = 0; r < kR; ++r) {
-                    const float *tr = a.near_rec + (size_t)t_of[r / (kR / kGroup)] * kRec32 * kTs +
-                                      (r % (kR / kGroup)) * kT + tid;
+                    const float *tr = c_near + (size_t)c_tile * kRec32 * kTs + r * kT + tid;
                     hx[r] = __ldg(tr);
                     hy[r] = __ldg(tr + kTs);
                     hz[r] = __ldg(tr + 2 * kTs);
@@ -263,7 +284,7 @@ __global__ void __launch_bounds__(kT, 8) br32_kernel(Args a)
                         const float rx = (shx - hx[r]) + (slx - lx[r]);
                         const float ry = (shy - hy[r]) + (sly - ly[r]);
                         const float rz = (shz - hz[r]) + (slz - lz[r]);
-                        const float q = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, a.d2)));
+                        const float q = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, c_d2)));
                         const float iq = dev::rsqrt_approx(q);
                         const float kk = iq * iq * iq;
                         px[r] = fmaf(kk, fmaf(ry, gz, -rz * gy), px[r]);
@@ -273,9 +294,9 @@ __global__ void __launch_bounds__(kT, 8) br32_kernel(Args a)
                 }
 #pragma unroll
                 for (int r = 0; r < kR; ++r) {
-                    acc[0][r][tid] += (double)px[r];
-                    acc[1][r][tid] += (double)py[r];
-                    acc[2][r][tid] += (double)pz[r];
+                    acc[0][r][tid] += __float2ll_rn(px[r] * c_mult);
+                    acc[1][r][tid] += __float2ll_rn(py[r] * c_mult);
+                    acc[2][r][tid] += __float2ll_rn(pz[r] * c_mult);
                 }
             }
         }
@@ -284,61 +305,28 @@ __global__ void __launch_bounds__(kT, 8) br32_kernel(Args a)
             kb = k;
             break;
         }
-        if (tid == 0 && k + 2 < nu) {
+        if (tid == 0) {
             dev::fence_proxy_async();
-            issue_unit(a, u0 + k + 2, stage[b], &flag[b], &bar[b]);
+            produce(b);  // unit k + 2 into the stage just consumed
         }
     }
     if (bad) {
         if (tid == 0) {
-            atomicOr(a.err, kErrTimeout);
-            for (int k = kb; k < kb + 2 && k < nu; ++k)
-                (void)dev::mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1);
+            atomicOr(err, kErrTimeout);
+            // let copies still in flight (units kb and kb + 1) land before shared memory is
+            // released, again with bounded waits
+            for (int k = kb; k < kb + 2; ++k)
+                if (unit[k & 1].inst >= 0) (void)dev::mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1);
         }
         return;
     }
-    if (cur_g >= 0) {
-        double *o = a.part + (size_t)(cta * a.kseg + (cur_g - g_first)) * 3 * (kGroup * kTs);
-#pragma unroll
-        for (int r = 0; r < kR; ++r) {
-            const int idx = (r / (kR / kGroup)) * kTs + (r % (kR / kGroup)) * kT + tid;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) o[c * (kGroup * kTs) + idx] = acc[c][r][tid];
-        }
-    }
-}
-
-// Sum the partials of every target in CTA order, write u in mesh order and Phi = q + |u|^2 / 2.
-__global__ void __launch_bounds__(256)
-    reduce32_kernel(Args a, const double *__restrict__ q, double *__restrict__ u, double *__restrict__ phi)
-{
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.N) return;
-    const int i = p / a.n2, j = p - (p / a.n2) * a.n2;
-    const int ti = i >> 4, tj = j >> 4;
-    const int G = ti * a.ng2 + tj / kGroup;
-    const int idx = (tj % kGroup) * kTs + ((i & 15) << 4) + (j & 15);
-    const long long first = (long long)G * a.ntiles, last = first + a.ntiles - 1;
-    const int c0 = cta_of_unit(first, a.units, a.ctas), c1 = cta_of_unit(last, a.units, a.ctas);
-    double s[3] = {0.0, 0.0, 0.0};
-    for (int c = c0; c <= c1; ++c) {
-        const long long st = (long long)c * a.units / a.ctas;
-        const int seg = G - (int)(st / a.ntiles);
-        const double *o = a.part + (size_t)(c * a.kseg + seg) * 3 * (kGroup * kTs) + idx;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) s[k] += o[k * (kGroup * kTs)];
-    }
-    const size_t N = a.N;
-    u[p] = s[0];
-    u[N + p] = s[1];
-    u[2 * N + p] = s[2];
-    phi[p] = q[p] + 0.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    flush();
 }
 
 // padding slots: zero strength and |s|^2 + delta^2 = delta^2, so they add exactly nothing
-__global__ void init_far_kernel(float *far_rec, size_t nslots_tiles, float d2)
+__global__ void init_far_kernel(float *far_rec, size_t ntiles, float d2)
 {
-    const size_t total = nslots_tiles * kRec32F * kTs;
+    const size_t total = ntiles * kRec32F * kTs;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
         const int row = (int)((e / kTs) % kRec32F);
@@ -346,71 +334,29 @@ __global__ void init_far_kernel(float *far_rec, size_t nslots_tiles, float d2)
     }
 }
 
-Args make_args(zm_ctx *c)
-{
-    Args a;
-    const Geom &g = c->geom;
-    const Tiling &t = c->tiling;
-    a.n1 = g.n1;
-    a.n2 = g.n2;
-    a.N = g.N;
-    a.nt2 = t.nt2;
-    a.ntiles = t.ntiles;
-    a.ng2 = (t.nt2 + kGroup - 1) / kGroup;
-    a.ngroups = t.nt1 * a.ng2;
-    a.units = (long long)a.ngroups * t.ntiles;
-    a.ctas = c->plan32.ctas;
-    a.kseg = c->plan32.kseg;
-    a.d2 = (float)(c->delta * c->delta);
-    a.near_rec = static_cast<const float *>(c->src);
-    a.far_rec = c->src_far;
-    a.tinfo = c->tinfo;
-    a.part = c->part;
-    a.err = c->err;
-    return a;
-}
-
 }  // namespace
 
-Br32Plan plan_br32(const Geom &g, const Tiling &t, int sm_count)
+int br32_occupancy()
 {
-    Br32Plan p;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, br32_kernel, kT, 0) != cudaSuccess || occ < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, br32_batch_kernel, kT, 0) != cudaSuccess ||
+        occ < 1) {
         cudaGetLastError();
         occ = 1;
     }
-    const int ng2 = (t.nt2 + kGroup - 1) / kGroup;
-    const long long units = (long long)t.nt1 * ng2 * t.ntiles;
-    p.ctas = (int)std::min<long long>(units, (long long)occ * sm_count);
-    const long long lmax = (units + p.ctas - 1) / p.ctas;
-    p.kseg = (int)((lmax - 1) / t.ntiles) + 2;
-    p.part_doubles = (size_t)p.ctas * p.kseg * 3 * kGroup * kTs;
-    p.occupancy = occ;
-    return p;
+    return occ;
 }
 
-int init_far_records(zm_ctx *c)
+void init_far_records(float *far_rec, int ntiles, float d2, cudaStream_t s)
 {
-    init_far_kernel<<<256, 256, 0, c->stream>>>(c->src_far, (size_t)c->tiling.ntiles,
-                                               (float)(c->delta * c->delta));
-    return cuda_check(cudaGetLastError(), "far-record init");
+    init_far_kernel<<<256, 256, 0, s>>>(far_rec, (size_t)ntiles, d2);
 }
 
-int launch_br32(zm_ctx *c)
+int launch_br32_batch(const Inst *d_insts, int ninst, long long nitems, int ctas,
+                      unsigned long long *counter, int *err, cudaStream_t s)
 {
-    const Args a = make_args(c);
-    cudaEvent_t ev = nullptr;
-    prof_begin(c, ZM_K_BR, &ev);
-    br32_kernel<<<a.ctas, kT, 0, c->stream>>>(a);
-    prof_end(c, ZM_K_BR, ev);
-    c->prof.pairs += (int64_t)a.N * (int64_t)a.N;
-    int rc = cuda_check(cudaGetLastError(), "Birkhoff-Rott FP32C kernel launch");
-    if (rc) return rc;
-    prof_begin(c, ZM_K_REDUCE, &ev);
-    reduce32_kernel<<<(a.N + 255) / 256, 256, 0, c->stream>>>(a, c->q, c->u, c->phi);
-    prof_end(c, ZM_K_REDUCE, ev);
-    return cuda_check(cudaGetLastError(), "Birkhoff-Rott FP32C reduction launch");
+    br32_batch_kernel<<<ctas, kT, 0, s>>>(d_insts, ninst, nitems, counter, err);
+    return cuda_check(cudaGetLastError(), "Birkhoff-Rott FP32C kernel launch");
 }
 
 }  // namespace zm

@@ -212,7 +212,7 @@ int launch_riesz(zm_ctx *c, const double *y)
     pass_c<<<g.n1 / ra, kFftTpb, ra * g.n2 * sizeof(double2), c->stream>>>(
         g.n1, g.n2, l2, ra, c->fb, c->tw2, c->nrm, c->q, c->u, c->phi);
     prof_end(c, ZM_K_FFT, ev);
-    c->prof.launches[ZM_K_FFT] += 2;  // three kernels per Riesz evaluation
+    c->prof.acc.launches[ZM_K_FFT] += 2;  // three kernels per Riesz evaluation
     return cuda_check(cudaGetLastError(), "Riesz FFT launch");
 }
 

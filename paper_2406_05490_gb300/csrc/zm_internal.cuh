@@ -55,6 +55,37 @@ struct Br32Plan {
 // Device-side status word bits.
 constexpr int kErrTimeout = 1;
 
+// Optional CUDA-event timing of every launch, per kernel class (see zm_set_profiling).
+struct Prof {
+    int on = 0;
+    zm_profile acc{};
+    struct Ev {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Ev> live;
+    std::vector<cudaEvent_t> pool;
+};
+
+// One interface as the batched kernels see it (a plain struct mirrored into device memory).
+struct Inst {
+    Geom geom;
+    Tiling tiling;
+    double atwood, g, mu, delta;
+    int block0;                 // first 256-thread block of this interface in the point kernels
+    int chunk, nchunks;         // source tiles per Birkhoff-Rott work item; items per target tile
+    long long item0;            // first Birkhoff-Rott work item of this interface
+    double *y[3];               // state and two RK3 stage buffers, 5N doubles each
+    double *u, *phi, *q;        // 3N, N, N
+    float *near_rec, *far_rec;  // [tile][9][256], [tile][10][256]
+    float4 *tinfo;              // [tile]: centre, radius
+    unsigned long long *ufix;   // [3][N] fixed-point velocity accumulators (two's complement)
+    unsigned int *gmax;         // float bits of max |gamma'| over the mesh
+    int *scale;                 // fixed-point scale (power of two) used by the last sum
+};
+
+class Batch;
+
 }  // namespace zm
 
 struct zm_ctx {
@@ -89,15 +120,8 @@ struct zm_ctx {
     int *err;   // device status word (zm::kErr*)
     int *flag;  // device scratch flag (finite check)
 
-    // profiling
-    int profiling;
-    zm_profile prof;
-    struct Ev {
-        int cls;
-        cudaEvent_t a, b;
-    };
-    std::vector<Ev> ev_live;
-    std::vector<cudaEvent_t> ev_pool;
+    zm::Prof prof;
+    zm::Batch *batch;  // FP32C high order: the interface lives in a batch of one
 };
 
 namespace zm {
@@ -107,8 +131,12 @@ int set_error(int code, const std::string &msg);
 int cuda_check(cudaError_t e, const char *what);
 
 // ---- profiling helpers (zm_api.cu) -----------------------------------------------------------
-void prof_begin(zm_ctx *c, int cls, cudaEvent_t *a);
-void prof_end(zm_ctx *c, int cls, cudaEvent_t a);
+void prof_begin(Prof &pr, cudaStream_t s, int cls, cudaEvent_t *a);
+void prof_end(Prof &pr, cudaStream_t s, int cls, cudaEvent_t a);
+void prof_fold(Prof &pr, cudaStream_t s);
+void prof_release(Prof &pr);
+inline void prof_begin(zm_ctx *c, int cls, cudaEvent_t *a) { prof_begin(c->prof, c->stream, cls, a); }
+inline void prof_end(zm_ctx *c, int cls, cudaEvent_t a) { prof_end(c->prof, c->stream, cls, a); }
 
 // ---- stencil kernels (zm_stencil.cu) -----------------------------------------------------------
 // Geometry pass over state y (5N): writes source records (high order), q, and normals (low).
@@ -127,10 +155,11 @@ BrPlan plan_br(const Geom &g, const Tiling &t, int sm_count);
 Tiling make_tiling(const Geom &g);
 int launch_br(zm_ctx *c, const double *y);  // FP64 path (then launch_reduce)
 
-// ---- FP32C Birkhoff-Rott kernels (zm_br32.cu) -----------------------------------------------------
-Br32Plan plan_br32(const Geom &g, const Tiling &t, int sm_count);
-int init_far_records(zm_ctx *c);
-int launch_br32(zm_ctx *c);  // sum + its reduction (u, Phi)
+// ---- FP32C Birkhoff-Rott kernel over a batch of interfaces (zm_br32.cu) ----------------------------
+int br32_occupancy();  // resident CTAs per SM of the batched kernel
+int launch_br32_batch(const Inst *d_insts, int ninst, long long nitems, int ctas,
+                      unsigned long long *counter, int *err, cudaStream_t s);
+void init_far_records(float *far_rec, int ntiles, float d2, cudaStream_t s);
 
 // ---- low order (zm_fft.cu) ---------------------------------------------------------------------
 int fft_setup(zm_ctx *c);

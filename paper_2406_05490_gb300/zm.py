@@ -87,6 +87,21 @@ def load():
             "zm_check_finite": (I, [VP]),
             "zm_measure_peak": (I, [I, ctypes.POINTER(D)]),
             "zm_br_velocity_noalloc": (I, [ctypes.c_int32, VP, VP, D, VP, VP, VP]),
+            "zm_batch_create": (I, [ctypes.c_int32, ctypes.POINTER(zm_mesh), ctypes.POINTER(D), D, D,
+                                    ctypes.POINTER(D), ctypes.POINTER(VP)]),
+            "zm_batch_set_stream": (I, [VP, VP]),
+            "zm_batch_set_state": (I, [VP, ctypes.c_int32, VP, VP]),
+            "zm_batch_get_state": (I, [VP, ctypes.c_int32, VP, VP]),
+            "zm_batch_velocity": (I, [VP]),
+            "zm_batch_get_velocity": (I, [VP, ctypes.c_int32, VP, VP]),
+            "zm_batch_step": (I, [VP, D, ctypes.c_int32]),
+            "zm_batch_sync": (I, [VP]),
+            "zm_batch_set_chunk": (I, [VP, ctypes.c_int32]),
+            "zm_batch_info": (I, [VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
+            "zm_batch_set_profiling": (I, [VP, I]),
+            "zm_batch_get_profile": (I, [VP, ctypes.POINTER(zm_profile)]),
+            "zm_batch_destroy": (None, [VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -198,6 +213,81 @@ def zm_br_velocity_noalloc(n, z, gamma, delta, u, status=None, stream=None):
     workspace is a static device array, shared by all calls; n <= 65536)."""
     _check(load().zm_br_velocity_noalloc(int(n), ptr(z), ptr(gamma), float(delta), ptr(u),
                                          None if status is None else status.data_ptr(), stream))
+
+
+def _profile_dict(p):
+    return {"ms": {KERNEL_NAMES[k]: p.ms[k] for k in range(ZM_K_COUNT)},
+            "launches": {KERNEL_NAMES[k]: int(p.launches[k]) for k in range(ZM_K_COUNT)},
+            "pairs": int(p.pairs)}
+
+
+def zm_batch_create(meshes, atwood, g=1.0, mu=0.0, delta=None):
+    """meshes: list of (n1, n2, L1, L2, periodic) tuples; atwood/delta: per-interface lists."""
+    lib = load()
+    k = len(meshes)
+    arr = (zm_mesh * k)(*[zm_mesh(int(m[0]), int(m[1]), float(m[2]), float(m[3]), int(bool(m[4])))
+                          for m in meshes])
+    if delta is None:
+        delta = [0.1 * m[2] / m[0] for m in meshes]
+    at = (ctypes.c_double * k)(*[float(a) for a in atwood])
+    de = (ctypes.c_double * k)(*[float(d) for d in delta])
+    h = VP()
+    _check(lib.zm_batch_create(k, arr, at, float(g), float(mu), de, ctypes.byref(h)))
+    return h
+
+
+def zm_batch_set_stream(h, stream):
+    _check(load().zm_batch_set_stream(h, stream))
+
+
+def zm_batch_set_state(h, index, z, w):
+    _check(load().zm_batch_set_state(h, int(index), ptr(z), ptr(w)))
+
+
+def zm_batch_get_state(h, index, z, w):
+    _check(load().zm_batch_get_state(h, int(index), ptr(z), ptr(w)))
+
+
+def zm_batch_velocity(h):
+    _check(load().zm_batch_velocity(h))
+
+
+def zm_batch_get_velocity(h, index, u, wdot=None):
+    _check(load().zm_batch_get_velocity(h, int(index), ptr(u), ptr(wdot)))
+
+
+def zm_batch_step(h, dt, nsteps):
+    _check(load().zm_batch_step(h, float(dt), int(nsteps)))
+
+
+def zm_batch_sync(h):
+    _check(load().zm_batch_sync(h))
+
+
+def zm_batch_set_chunk(h, chunk):
+    _check(load().zm_batch_set_chunk(h, int(chunk)))
+
+
+def zm_batch_info(h):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    d = ctypes.c_int32()
+    _check(load().zm_batch_info(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return {"points": a.value, "pairs_per_eval": b.value, "work_items": c.value, "ctas": d.value}
+
+
+def zm_batch_set_profiling(h, on):
+    _check(load().zm_batch_set_profiling(h, int(bool(on))))
+
+
+def zm_batch_get_profile(h):
+    p = zm_profile()
+    _check(load().zm_batch_get_profile(h, ctypes.byref(p)))
+    return _profile_dict(p)
+
+
+def zm_batch_destroy(h):
+    if h:
+        load().zm_batch_destroy(h)
 
 
 # ---- a small convenience wrapper -------------------------------------------------------------

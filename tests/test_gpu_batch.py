@@ -1,0 +1,110 @@
+"""Batched form (many interfaces of uneven sizes in one set of launches per RK3 stage).
+
+Checks: every interface against the CPU oracle (FP32C tolerance 1e-6 relative L2), results of
+an interface alone and inside a mixed batch (bitwise equal: the cross-tile accumulation is exact
+fixed point, so neither the batch composition nor the work-item size changes a bit), and RK3
+stepping of the batch against the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_05490_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-6
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+SPECS = [(37, 53, False, 0.4, 1), (64, 64, True, 0.6, 2), (48, 40, True, 0.3, 3), (16, 16, False, 0.7, 4),
+         (5, 9, False, 0.5, 5), (80, 96, True, 0.25, 6)]
+
+
+@pytest.fixture(scope="module")
+def zm():
+    import torch
+    from paper_2406_05490_gb300 import zm as _zm
+    assert torch.cuda.is_available()
+    _zm.load()
+    return _zm
+
+
+def make_batch(zm, specs):
+    meshes = [(n1, n2, 1.0, 1.0, per) for n1, n2, per, _, _ in specs]
+    atw = [a for _, _, _, a, _ in specs]
+    delta = [0.1 / max(n1, n2) for n1, n2, _, _, _ in specs]
+    return zm.zm_batch_create(meshes, atw, g=1.3, mu=0.0, delta=delta), delta
+
+
+def test_batch_velocity_parity_and_mix_invariance(zm):
+    h, delta = make_batch(zm, SPECS)
+    states = [inputs.random_state(n1, n2, seed=s) for n1, n2, _, _, s in SPECS]
+    for k, (z, w) in enumerate(states):
+        zm.zm_batch_set_state(h, k, z, w)
+    zm.zm_batch_velocity(h)
+    outs = []
+    for k, (n1, n2, per, at, s) in enumerate(SPECS):
+        N = n1 * n2
+        u = np.empty((3, N))
+        wd = np.empty((2, N))
+        zm.zm_batch_get_velocity(h, k, u, wd)
+        outs.append((u, wd))
+        m = oracle.Mesh(n1, n2, periodic=per)
+        u_ref, wd_ref = oracle.derivative(m, states[k][0], states[k][1], at, 1.3, 0.0, delta[k])
+        eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+        print(f"batch[{k}] {n1}x{n2}: rel L2 u={eu:.3e} wdot={ew:.3e}")
+        assert eu <= TOL32 and ew <= TOL32
+    # a different work-item size reorders all accumulation: results must not change by a bit
+    zm.zm_batch_set_chunk(h, 1)
+    zm.zm_batch_velocity(h)
+    for k, (n1, n2, _, _, _) in enumerate(SPECS):
+        u = np.empty((3, n1 * n2))
+        zm.zm_batch_get_velocity(h, k, u, None)
+        assert np.array_equal(u, outs[k][0])
+    zm.zm_batch_destroy(h)
+    # each interface alone (a context of its own) gives the same bits as inside the mix
+    for k, (n1, n2, per, at, s) in enumerate(SPECS):
+        model = zm.ZModel(n1, n2, periodic=per, atwood=at, g=1.3, delta=delta[k], fp32c=True)
+        u, wd = model.velocity(*states[k])
+        model.close()
+        assert np.array_equal(u, outs[k][0]) and np.array_equal(wd, outs[k][1])
+
+
+def test_batch_steps_match_oracle_and_alone(zm):
+    specs = SPECS[:4]
+    h, delta = make_batch(zm, specs)
+    init = [inputs.multi_mode(n1, n_modes=4, seed=s, amp_std=0.02) if n1 == n2 else
+            inputs.random_state(n1, n2, seed=s) for n1, n2, _, _, s in specs]
+    for k, (z, w) in enumerate(init):
+        zm.zm_batch_set_state(h, k, z, w)
+    zm.zm_batch_step(h, 2e-3, 3)
+    zm.zm_batch_sync(h)
+    for k, (n1, n2, per, at, s) in enumerate(specs):
+        z1 = np.empty((3, n1 * n2))
+        w1 = np.empty((2, n1 * n2))
+        zm.zm_batch_get_state(h, k, z1, w1)
+        m = oracle.Mesh(n1, n2, periodic=per)
+        zr, wr = oracle.run(m, init[k][0], init[k][1], at, 1.3, 0.0, delta[k], 2e-3, 3)
+        ez, ew = rel(z1, zr), rel(w1, wr)
+        print(f"batch step[{k}] {n1}x{n2}: rel L2 z={ez:.3e} w={ew:.3e}")
+        assert ez <= TOL32 and ew <= TOL32
+        model = zm.ZModel(n1, n2, periodic=per, atwood=at, g=1.3, delta=delta[k], fp32c=True)
+        model.set_state(*init[k])
+        model.step(2e-3, 3)
+        za, wa = model.get_state()
+        model.close()
+        assert np.array_equal(za, z1) and np.array_equal(wa, w1)
+    zm.zm_batch_destroy(h)
+
+
+def test_batch_rejects_bad_arguments(zm):
+    with pytest.raises(zm.ZMError) as e:
+        zm.zm_batch_create([(4, 4, 1.0, 1.0, True)], [0.5])
+    assert e.value.code == zm.ZM_ERR_INVALID
+    with pytest.raises(zm.ZMError) as e:
+        zm.zm_batch_create([(16, 16, 1.0, 1.0, True)], [0.5], delta=[0.0])
+    assert e.value.code == zm.ZM_ERR_INVALID

@@ -179,6 +179,56 @@ int zm_batch_set_profiling(zm_batch *b, int on);
 int zm_batch_get_profile(zm_batch *b, zm_profile *out);
 void zm_batch_destroy(zm_batch *b);
 
+/* ---- serving: continuous batching of solve requests ------------------------------------- */
+
+/* A worker thread owned by the server admits submitted requests in arrival order as slots
+ * (max_slots) and device memory (mem_budget_bytes, counted per request from its mesh size)
+ * free up, keeps every admitted interface's state resident, advances all resident interfaces
+ * together by one RK3 step per iteration (the batched FP32C path) and retires finished ones
+ * between iterations, so requests arriving while others run join the next iteration.  A
+ * request's result does not depend on the others (bitwise).  The paper has no serving form. */
+#define ZM_REQ_QUEUED 0
+#define ZM_REQ_RUNNING 1
+#define ZM_REQ_DONE 2
+#define ZM_REQ_FAILED 3
+
+typedef struct zm_server zm_server;
+
+typedef struct {
+    int64_t iterations;    /* loop iterations that ran on the GPU                              */
+    int64_t steps;         /* batched RK3 steps                                                */
+    int64_t pairs;         /* Birkhoff-Rott pair interactions evaluated                        */
+    int64_t completed, failed, queued, running, peak_running;
+    int64_t bytes_in_use, peak_bytes; /* device bytes held by admitted requests              */
+    double busy_s;         /* wall time spent in GPU iterations                               */
+} zm_server_stats;
+
+/* Start a server on the current device (its own stream and worker thread). */
+int zm_server_create(size_t mem_budget_bytes, int32_t max_slots, double g, double mu,
+                     zm_server **out);
+/* Queue a solve: mesh, Atwood number, core size delta > 0, step dt, nsteps SSP-RK3 steps, and
+ * the initial state (host pointers, copied before return).  *id receives the request id.
+ * ZM_ERR_BUSY if the request alone exceeds the memory budget. */
+int zm_server_submit(zm_server *s, const zm_mesh *mesh, double atwood, double delta, double dt,
+                     int32_t nsteps, const double *z, const double *w, int64_t *id);
+/* Device bytes one request of this mesh holds while admitted (what the budget counts). */
+int zm_server_request_bytes(const zm_mesh *mesh, size_t *bytes);
+/* Current state of a request (ZM_REQ_*). */
+int zm_server_poll(zm_server *s, int64_t id, int32_t *state);
+/* Block until the request finished (timeout_s < 0: no limit); returns its status, or
+ * ZM_ERR_TIMEOUT if the host-side wait ran out. */
+int zm_server_wait(zm_server *s, int64_t id, double timeout_s);
+/* Copy a finished request's final state (host pointers, may be NULL), its latency from submit
+ * to completion and its queueing time from submit to admission (seconds), and release the
+ * request.  Returns the request's status (ZM_ERR_NONFINITE if its state blew up). */
+int zm_server_result(zm_server *s, int64_t id, double *z, double *w, double *latency_s,
+                     double *queue_s);
+/* Cancel a request: a queued one fails at once, a running one leaves at the next iteration. */
+int zm_server_cancel(zm_server *s, int64_t id);
+int zm_server_get_stats(zm_server *s, zm_server_stats *out);
+/* Stop the worker and free everything (requests still queued or running are dropped). */
+void zm_server_destroy(zm_server *s);
+
 /* ---- Birkhoff-Rott sum without allocation ------------------------------------------------ */
 
 /* The paper has no counterpart: this entry point exists for callers that cannot allocate GPU

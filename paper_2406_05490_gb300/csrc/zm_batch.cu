@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "zm_batch.cuh"
 #include "zm_stencil.cuh"
 
 namespace zm {
@@ -58,285 +59,325 @@ __global__ void __launch_bounds__(kPtb)
 template <int kMode>
 __global__ void __launch_bounds__(kPtb)
     batch_vorticity_kernel(const Inst *__restrict__ insts, const int *__restrict__ block_inst, int yin,
-                           int yout, double dt, double ca, double cb)
+                           int yout, double ca, double cb)
 {
     const Inst &I = insts[block_inst[blockIdx.x]];
     const int p = (blockIdx.x - I.block0) * kPtb + threadIdx.x;
     if (p >= I.geom.N) return;
     if (I.mu != 0.0)
-        vorticity_point<true, kMode>(I.geom, p, I.phi, I.y[yin], I.u, I.atwood, I.mu, dt, ca, cb,
+        vorticity_point<true, kMode>(I.geom, p, I.phi, I.y[yin], I.u, I.atwood, I.mu, I.dt, ca, cb,
                                      I.y[0], I.y[yout], I.y[2]);
     else
-        vorticity_point<false, kMode>(I.geom, p, I.phi, I.y[yin], I.u, I.atwood, I.mu, dt, ca, cb,
+        vorticity_point<false, kMode>(I.geom, p, I.phi, I.y[yin], I.u, I.atwood, I.mu, I.dt, ca, cb,
                                       I.y[0], I.y[yout], I.y[2]);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// sizes of the pieces of one interface's slab, in order
+void slab_layout(const zm_mesh &m, size_t sz[12])
+{
+    const size_t N = (size_t)m.n1 * m.n2;
+    const size_t nt = (size_t)((m.n1 + 15) / 16) * ((m.n2 + 15) / 16);
+    const size_t slots = nt * 256;
+    const size_t s[12] = {5 * N * 8, 5 * N * 8, 5 * N * 8, 3 * N * 8, N * 8, N * 8, 3 * N * 8,
+                          slots * kRec32 * 4, slots * kRec32F * 4, nt * 16, 4, 4};
+    for (int k = 0; k < 12; ++k) sz[k] = s[k];
+}
+
+int default_chunk(int ntiles) { return std::max(1, std::min(8, ntiles / 16)); }
+
 }  // namespace
 
-class Batch {
-public:
-    int count = 0;
-    std::vector<Inst> h;
-    Inst *d = nullptr;
-    int *block_inst = nullptr;
-    int nblocks = 0;
-    long long nitems = 0;
-    int ctas = 0, occ = 1, sms = 152;
-    unsigned long long *counter = nullptr;
-    int *err = nullptr;
-    std::vector<void *> slabs;
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap = nullptr;  // private stream for graph capture
-    cudaGraphExec_t gexec = nullptr;
-    double gdt = 0.0;
-    Prof own;
-    Prof *prof = &own;
-    int device = 0;
+void Batch::release()
+{
+    // the stream is borrowed (context's, caller's or server's): synchronise it once and forget
+    // it, so that a second release never touches a stream its owner has destroyed
+    if (stream) cudaStreamSynchronize(stream);
+    stream = nullptr;
+    drop_graph();
+    if (cap) cudaStreamDestroy(cap);
+    cap = nullptr;
+    for (void *s : owned) cudaFree(s);
+    owned.clear();
+    if (d) cudaFree(d);
+    if (block_inst) cudaFree(block_inst);
+    if (counter) cudaFree(counter);
+    if (err) cudaFree(err);
+    d = nullptr;
+    block_inst = nullptr;
+    counter = nullptr;
+    err = nullptr;
+    d_cap = bi_cap = 0;
+    prof_release(own);
+}
 
-    ~Batch() { release(); }
+size_t Batch::inst_bytes(const zm_mesh &m)
+{
+    size_t sz[12], total = 0;
+    slab_layout(m, sz);
+    for (int k = 0; k < 12; ++k) total += align256(sz[k]);
+    return total;
+}
 
-    void release()
-    {
-        if (stream) cudaStreamSynchronize(stream);
-        if (gexec) cudaGraphExecDestroy(gexec);
-        gexec = nullptr;
-        if (cap) cudaStreamDestroy(cap);
-        cap = nullptr;
-        for (void *s : slabs) cudaFree(s);
-        slabs.clear();
+int Batch::alloc_inst(Inst &I, const zm_mesh &m, double atwood, double g, double mu, double delta,
+                      double dt, cudaStream_t s, bool async, void **slab_out)
+{
+    std::memset(&I, 0, sizeof(I));
+    I.geom.n1 = m.n1;
+    I.geom.n2 = m.n2;
+    I.geom.N = m.n1 * m.n2;
+    I.geom.L1 = m.L1;
+    I.geom.L2 = m.L2;
+    I.geom.dx1 = m.L1 / m.n1;
+    I.geom.dx2 = m.L2 / m.n2;
+    I.geom.periodic = m.periodic ? 1 : 0;
+    I.tiling = make_tiling(I.geom);
+    I.atwood = atwood;
+    I.g = g;
+    I.mu = mu;
+    I.delta = delta;
+    I.dt = dt;
+    size_t sz[12], off[12], total = 0;
+    slab_layout(m, sz);
+    for (int k = 0; k < 12; ++k) {
+        off[k] = total;
+        total += align256(sz[k]);
+    }
+    void *slab = nullptr;
+    cudaError_t e = async ? cudaMallocAsync(&slab, total, s) : cudaMalloc(&slab, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ZM_ERR_NOMEM, "interface state: device allocation failed");
+    }
+    e = async ? cudaMemsetAsync(slab, 0, total, s) : cudaMemset(slab, 0, total);
+    if (e != cudaSuccess) return set_error(ZM_ERR_CUDA, "interface state: memset failed");
+    char *b = static_cast<char *>(slab);
+    for (int k = 0; k < 3; ++k) I.y[k] = reinterpret_cast<double *>(b + off[k]);
+    I.u = reinterpret_cast<double *>(b + off[3]);
+    I.phi = reinterpret_cast<double *>(b + off[4]);
+    I.q = reinterpret_cast<double *>(b + off[5]);
+    I.ufix = reinterpret_cast<unsigned long long *>(b + off[6]);
+    I.near_rec = reinterpret_cast<float *>(b + off[7]);
+    I.far_rec = reinterpret_cast<float *>(b + off[8]);
+    I.tinfo = reinterpret_cast<float4 *>(b + off[9]);
+    I.gmax = reinterpret_cast<unsigned int *>(b + off[10]);
+    I.scale = reinterpret_cast<int *>(b + off[11]);
+    init_far_records(I.far_rec, I.tiling.ntiles, (float)(delta * delta), async ? s : nullptr);
+    *slab_out = slab;
+    return cuda_check(cudaGetLastError(), "interface state init");
+}
+
+int Batch::setup()
+{
+    cudaGetDevice(&device);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    occ = br32_occupancy();
+    if (cudaMalloc(&counter, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ZM_ERR_NOMEM, "batch: device allocation failed");
+    }
+    cudaMemset(counter, 0, sizeof(unsigned long long));
+    cudaMemset(err, 0, sizeof(int));
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+        return set_error(ZM_ERR_CUDA, "batch: stream creation failed");
+    return cuda_check(cudaDeviceSynchronize(), "batch setup");
+}
+
+int Batch::init(int n, const zm_mesh *meshes, const double *atwood, double g, double mu,
+                const double *delta)
+{
+    int rc = setup();
+    if (rc) return rc;
+    h.resize(n);
+    for (int k = 0; k < n; ++k) {
+        void *slab = nullptr;
+        rc = alloc_inst(h[k], meshes[k], atwood[k], g, mu, delta[k], 0.0, nullptr, false, &slab);
+        if (rc) return rc;
+        owned.push_back(slab);
+    }
+    rc = plan();
+    if (rc) return rc;
+    return cuda_check(cudaDeviceSynchronize(), "batch init");
+}
+
+int Batch::plan()
+{
+    drop_graph();
+    long long items = 0;
+    int blocks = 0;
+    for (auto &I : h) {
+        I.block0 = blocks;
+        blocks += (I.geom.N + kPtb - 1) / kPtb;
+        I.chunk = chunk_override > 0 ? std::min(chunk_override, I.tiling.ntiles)
+                                     : default_chunk(I.tiling.ntiles);
+        I.nchunks = (I.tiling.ntiles + I.chunk - 1) / I.chunk;
+        I.item0 = items;
+        items += (long long)I.tiling.ntiles * I.nchunks;
+    }
+    nblocks = blocks;
+    nitems = items;
+    ctas = (int)std::max<long long>(1, std::min<long long>(nitems, (long long)occ * sms));
+    const int n = (int)h.size();
+    if (n == 0) return ZM_OK;
+    bi_host.resize(nblocks);
+    for (int k = 0; k < n; ++k) {
+        const int nb = (h[k].geom.N + kPtb - 1) / kPtb;
+        for (int q = 0; q < nb; ++q) bi_host[h[k].block0 + q] = k;
+    }
+    if (n > d_cap) {
         if (d) cudaFree(d);
-        if (block_inst) cudaFree(block_inst);
-        if (counter) cudaFree(counter);
-        if (err) cudaFree(err);
-        d = nullptr;
-        block_inst = nullptr;
-        counter = nullptr;
-        err = nullptr;
-        prof_release(own);
-    }
-
-    static int default_chunk(int ntiles) { return std::max(1, std::min(8, ntiles / 16)); }
-
-    int init(int n, const zm_mesh *meshes, const double *atwood, double g, double mu,
-             const double *delta)
-    {
-        count = n;
-        cudaGetDevice(&device);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-        occ = br32_occupancy();
-        h.resize(n);
-        long long items = 0;
-        int blocks = 0;
-        for (int k = 0; k < n; ++k) {
-            Inst &I = h[k];
-            std::memset(&I, 0, sizeof(I));
-            const zm_mesh &m = meshes[k];
-            I.geom.n1 = m.n1;
-            I.geom.n2 = m.n2;
-            I.geom.N = m.n1 * m.n2;
-            I.geom.L1 = m.L1;
-            I.geom.L2 = m.L2;
-            I.geom.dx1 = m.L1 / m.n1;
-            I.geom.dx2 = m.L2 / m.n2;
-            I.geom.periodic = m.periodic ? 1 : 0;
-            I.tiling = make_tiling(I.geom);
-            I.atwood = atwood[k];
-            I.g = g;
-            I.mu = mu;
-            I.delta = delta[k];
-            I.block0 = blocks;
-            blocks += (I.geom.N + kPtb - 1) / kPtb;
-            I.chunk = default_chunk(I.tiling.ntiles);
-            I.nchunks = (I.tiling.ntiles + I.chunk - 1) / I.chunk;
-            I.item0 = items;
-            items += (long long)I.tiling.ntiles * I.nchunks;
-            // one slab per interface
-            const size_t N = I.geom.N, slots = (size_t)I.tiling.ntiles * I.tiling.ts;
-            size_t off[12], total = 0;
-            const size_t sz[12] = {5 * N * 8, 5 * N * 8, 5 * N * 8, 3 * N * 8, N * 8, N * 8, 3 * N * 8,
-                                   slots * kRec32 * 4, slots * kRec32F * 4,
-                                   (size_t)I.tiling.ntiles * 16, 4, 4};
-            for (int s = 0; s < 12; ++s) {
-                off[s] = total;
-                total += align256(sz[s]);
-            }
-            void *slab = nullptr;
-            if (cudaMalloc(&slab, total) != cudaSuccess) {
-                cudaGetLastError();
-                return set_error(ZM_ERR_NOMEM, "batch: device allocation failed");
-            }
-            slabs.push_back(slab);
-            char *b = static_cast<char *>(slab);
-            if (cudaMemset(slab, 0, total) != cudaSuccess)
-                return set_error(ZM_ERR_CUDA, "batch: memset failed");
-            for (int s = 0; s < 3; ++s) I.y[s] = reinterpret_cast<double *>(b + off[s]);
-            I.u = reinterpret_cast<double *>(b + off[3]);
-            I.phi = reinterpret_cast<double *>(b + off[4]);
-            I.q = reinterpret_cast<double *>(b + off[5]);
-            I.ufix = reinterpret_cast<unsigned long long *>(b + off[6]);
-            I.near_rec = reinterpret_cast<float *>(b + off[7]);
-            I.far_rec = reinterpret_cast<float *>(b + off[8]);
-            I.tinfo = reinterpret_cast<float4 *>(b + off[9]);
-            I.gmax = reinterpret_cast<unsigned int *>(b + off[10]);
-            I.scale = reinterpret_cast<int *>(b + off[11]);
-            init_far_records(I.far_rec, I.tiling.ntiles, (float)(I.delta * I.delta), nullptr);
-        }
-        nblocks = blocks;
-        nitems = items;
-        ctas = (int)std::min<long long>(nitems, (long long)occ * sms);
-        std::vector<int> bi(nblocks);
-        for (int k = 0; k < n; ++k) {
-            const int nb = (h[k].geom.N + kPtb - 1) / kPtb;
-            for (int q = 0; q < nb; ++q) bi[h[k].block0 + q] = k;
-        }
-        if (cudaMalloc(&d, n * sizeof(Inst)) != cudaSuccess ||
-            cudaMalloc(&block_inst, nblocks * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&counter, sizeof(unsigned long long)) != cudaSuccess ||
-            cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+        d_cap = std::max(n, 2 * d_cap);
+        if (cudaMalloc(&d, d_cap * sizeof(Inst)) != cudaSuccess) {
             cudaGetLastError();
-            return set_error(ZM_ERR_NOMEM, "batch: device allocation failed");
+            d = nullptr;
+            d_cap = 0;
+            return set_error(ZM_ERR_NOMEM, "batch: descriptor allocation failed");
         }
-        cudaMemcpy(block_inst, bi.data(), nblocks * sizeof(int), cudaMemcpyHostToDevice);
-        cudaMemset(counter, 0, sizeof(unsigned long long));
-        cudaMemset(err, 0, sizeof(int));
-        int rc = upload();
+    }
+    if (nblocks > bi_cap) {
+        if (block_inst) cudaFree(block_inst);
+        bi_cap = std::max(nblocks, 2 * bi_cap);
+        if (cudaMalloc(&block_inst, bi_cap * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            block_inst = nullptr;
+            bi_cap = 0;
+            return set_error(ZM_ERR_NOMEM, "batch: block table allocation failed");
+        }
+    }
+    // stream-ordered after earlier work that read the old tables; the host vectors stay alive
+    // until the next plan(), which first synchronises the stream
+    cudaStreamSynchronize(stream);
+    int rc = cuda_check(cudaMemcpyAsync(d, h.data(), n * sizeof(Inst), cudaMemcpyHostToDevice, stream),
+                        "batch descriptor upload");
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(block_inst, bi_host.data(), nblocks * sizeof(int),
+                                             cudaMemcpyHostToDevice, stream),
+                             "batch block table upload");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(stream), "batch plan");
+    return rc;
+}
+
+int Batch::set_chunk(int chunk)
+{
+    chunk_override = chunk;
+    return plan();
+}
+
+int Batch::set_dt(double dt)
+{
+    bool changed = false;
+    for (auto &I : h)
+        if (I.dt != dt) {
+            I.dt = dt;
+            changed = true;
+        }
+    return changed ? plan() : ZM_OK;
+}
+
+void Batch::drop_graph()
+{
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+}
+
+int Batch::derivative(int yin, cudaStream_t s)
+{
+    if (h.empty()) return ZM_OK;
+    cudaEvent_t ev = nullptr;
+    prof_begin(*prof, s, ZM_K_GEOMETRY, &ev);
+    batch_geometry_kernel<<<nblocks, kPtb, 0, s>>>(d, block_inst, yin);
+    prof_end(*prof, s, ZM_K_GEOMETRY, ev);
+    int rc = cuda_check(cudaGetLastError(), "batch geometry launch");
+    if (rc) return rc;
+    prof_begin(*prof, s, ZM_K_BR, &ev);
+    rc = launch_br32_batch(d, (int)h.size(), nitems, ctas, counter, err, s);
+    prof_end(*prof, s, ZM_K_BR, ev);
+    for (auto &I : h) prof->acc.pairs += (int64_t)I.geom.N * I.geom.N;
+    if (rc) return rc;
+    prof_begin(*prof, s, ZM_K_REDUCE, &ev);
+    batch_finish_kernel<<<nblocks, kPtb, 0, s>>>(d, block_inst, counter);
+    prof_end(*prof, s, ZM_K_REDUCE, ev);
+    return cuda_check(cudaGetLastError(), "batch finish launch");
+}
+
+int Batch::vorticity(int yin, int mode, int yout, double ca, double cb, cudaStream_t s)
+{
+    if (h.empty()) return ZM_OK;
+    cudaEvent_t ev = nullptr;
+    prof_begin(*prof, s, ZM_K_VORT, &ev);
+    if (mode == 0)
+        batch_vorticity_kernel<0><<<nblocks, kPtb, 0, s>>>(d, block_inst, yin, yout, ca, cb);
+    else
+        batch_vorticity_kernel<1><<<nblocks, kPtb, 0, s>>>(d, block_inst, yin, yout, ca, cb);
+    prof_end(*prof, s, ZM_K_VORT, ev);
+    return cuda_check(cudaGetLastError(), "batch vorticity launch");
+}
+
+// SSP-RK3 (Shu-Osher): stage st writes ca y0 + cb (y_st + dt L(y_st)), dt per interface.
+int Batch::rk3_step_launches(cudaStream_t s)
+{
+    static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    static const int yin[3] = {0, 1, 2}, yout[3] = {1, 2, 0};
+    for (int st = 0; st < 3; ++st) {
+        int rc = derivative(yin[st], s);
+        if (!rc) rc = vorticity(yin[st], 1, yout[st], ca[st], cb[st], s);
         if (rc) return rc;
-        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
-            return set_error(ZM_ERR_CUDA, "batch: stream creation failed");
-        return cuda_check(cudaDeviceSynchronize(), "batch init");
     }
+    return ZM_OK;
+}
 
-    int upload()
-    {
-        return cuda_check(cudaMemcpy(d, h.data(), count * sizeof(Inst), cudaMemcpyHostToDevice),
-                          "batch descriptor upload");
-    }
-
-    // Work-item size (source tiles per item) for every interface; invalidates the step graph.
-    int set_chunk(int chunk)
-    {
-        long long items = 0;
-        for (auto &I : h) {
-            I.chunk = chunk > 0 ? std::min(chunk, I.tiling.ntiles) : default_chunk(I.tiling.ntiles);
-            I.nchunks = (I.tiling.ntiles + I.chunk - 1) / I.chunk;
-            I.item0 = items;
-            items += (long long)I.tiling.ntiles * I.nchunks;
-        }
-        nitems = items;
-        ctas = (int)std::min<long long>(nitems, (long long)occ * sms);
-        drop_graph();
-        cudaStreamSynchronize(stream);
-        return upload();
-    }
-
-    void drop_graph()
-    {
-        if (gexec) cudaGraphExecDestroy(gexec);
-        gexec = nullptr;
-    }
-
-    // One evaluation of L on y[yin] of every interface: u and Phi of each interface.
-    int derivative(int yin, cudaStream_t s)
-    {
-        cudaEvent_t ev = nullptr;
-        prof_begin(*prof, s, ZM_K_GEOMETRY, &ev);
-        batch_geometry_kernel<<<nblocks, kPtb, 0, s>>>(d, block_inst, yin);
-        prof_end(*prof, s, ZM_K_GEOMETRY, ev);
-        int rc = cuda_check(cudaGetLastError(), "batch geometry launch");
-        if (rc) return rc;
-        prof_begin(*prof, s, ZM_K_BR, &ev);
-        rc = launch_br32_batch(d, count, nitems, ctas, counter, err, s);
-        prof_end(*prof, s, ZM_K_BR, ev);
-        for (auto &I : h) prof->acc.pairs += (int64_t)I.geom.N * I.geom.N;
-        if (rc) return rc;
-        prof_begin(*prof, s, ZM_K_REDUCE, &ev);
-        batch_finish_kernel<<<nblocks, kPtb, 0, s>>>(d, block_inst, counter);
-        prof_end(*prof, s, ZM_K_REDUCE, ev);
-        return cuda_check(cudaGetLastError(), "batch finish launch");
-    }
-
-    int vorticity(int yin, int mode, double dt, double ca, double cb, int yout, cudaStream_t s)
-    {
-        cudaEvent_t ev = nullptr;
-        prof_begin(*prof, s, ZM_K_VORT, &ev);
-        if (mode == 0)
-            batch_vorticity_kernel<0><<<nblocks, kPtb, 0, s>>>(d, block_inst, yin, yout, dt, ca, cb);
-        else
-            batch_vorticity_kernel<1><<<nblocks, kPtb, 0, s>>>(d, block_inst, yin, yout, dt, ca, cb);
-        prof_end(*prof, s, ZM_K_VORT, ev);
-        return cuda_check(cudaGetLastError(), "batch vorticity launch");
-    }
-
-    // SSP-RK3 (Shu-Osher): stage st writes ca y0 + cb (y_st + dt L(y_st)).
-    int rk3_step_launches(double dt, cudaStream_t s)
-    {
-        static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
-        static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
-        static const int yin[3] = {0, 1, 2}, yout[3] = {1, 2, 0};
-        for (int st = 0; st < 3; ++st) {
-            int rc = derivative(yin[st], s);
-            if (!rc) rc = vorticity(yin[st], 1, dt, ca[st], cb[st], yout[st], s);
-            if (rc) return rc;
-        }
-        return ZM_OK;
-    }
-
-    int step(double dt, int nsteps)
-    {
-        if (nsteps <= 0) return ZM_OK;
-        if (prof->on) {  // event timing needs plain launches
-            for (int k = 0; k < nsteps; ++k) {
-                int rc = rk3_step_launches(dt, stream);
-                if (rc) return rc;
-            }
-            return ZM_OK;
-        }
-        if (!gexec || gdt != dt) {
-            drop_graph();
-            cudaGraph_t graph = nullptr;
-            int rc = cuda_check(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal),
-                                "step graph capture");
-            if (rc) return rc;
-            rc = rk3_step_launches(dt, cap);
-            cudaError_t e = cudaStreamEndCapture(cap, &graph);
-            if (rc) {
-                if (graph) cudaGraphDestroy(graph);
-                return rc;
-            }
-            rc = cuda_check(e, "step graph capture end");
-            if (!rc) rc = cuda_check(cudaGraphInstantiate(&gexec, graph, 0), "step graph instantiate");
-            if (graph) cudaGraphDestroy(graph);
-            if (rc) return rc;
-            gdt = dt;
-        }
+int Batch::step(int nsteps, bool use_graph)
+{
+    if (nsteps <= 0 || h.empty()) return ZM_OK;
+    if (prof->on || !use_graph) {  // event timing needs plain launches
         for (int k = 0; k < nsteps; ++k) {
-            int rc = cuda_check(cudaGraphLaunch(gexec, stream), "step graph launch");
+            int rc = rk3_step_launches(stream);
             if (rc) return rc;
         }
-        // launches inside the graph, for the launch counters (4 per stage)
-        prof->acc.launches[ZM_K_GEOMETRY] += 3LL * nsteps;
-        prof->acc.launches[ZM_K_BR] += 3LL * nsteps;
-        prof->acc.launches[ZM_K_REDUCE] += 3LL * nsteps;
-        prof->acc.launches[ZM_K_VORT] += 3LL * nsteps;
-        for (auto &I : h) prof->acc.pairs += 3LL * nsteps * (int64_t)I.geom.N * I.geom.N;
         return ZM_OK;
     }
-
-    int status()
-    {
-        int hs = 0;
-        int rc = cuda_check(cudaMemcpyAsync(&hs, err, sizeof(int), cudaMemcpyDeviceToHost, stream),
-                            "batch status read");
-        if (!rc) rc = cuda_check(cudaStreamSynchronize(stream), "batch synchronize");
-        if (!rc && (hs & kErrTimeout)) {
-            cudaMemsetAsync(err, 0, sizeof(int), stream);
-            rc = set_error(ZM_ERR_TIMEOUT, "a bounded device-side wait gave up (status word set)");
+    if (!gexec) {
+        cudaGraph_t graph = nullptr;
+        int rc = cuda_check(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal),
+                            "step graph capture");
+        if (rc) return rc;
+        rc = rk3_step_launches(cap);
+        cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
         }
-        return rc;
+        rc = cuda_check(e, "step graph capture end");
+        if (!rc) rc = cuda_check(cudaGraphInstantiate(&gexec, graph, 0), "step graph instantiate");
+        if (graph) cudaGraphDestroy(graph);
+        if (rc) return rc;
+        // the capture counted launches and pairs of one step; those launches never ran
+        for (int k = 0; k < ZM_K_COUNT; ++k) prof->acc.launches[k] -= (k == ZM_K_FFT) ? 0 : 3;
+        for (auto &I : h) prof->acc.pairs -= 3LL * I.geom.N * I.geom.N;
     }
-};
+    for (int k = 0; k < nsteps; ++k) {
+        int rc = cuda_check(cudaGraphLaunch(gexec, stream), "step graph launch");
+        if (rc) return rc;
+    }
+    for (int k = 0; k < ZM_K_COUNT; ++k) prof->acc.launches[k] += (k == ZM_K_FFT) ? 0 : 3LL * nsteps;
+    for (auto &I : h) prof->acc.pairs += 3LL * nsteps * (int64_t)I.geom.N * I.geom.N;
+    return ZM_OK;
+}
+
+int Batch::status()
+{
+    int hs = 0;
+    int rc = cuda_check(cudaMemcpyAsync(&hs, err, sizeof(int), cudaMemcpyDeviceToHost, stream),
+                        "batch status read");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(stream), "batch synchronize");
+    if (!rc && (hs & kErrTimeout)) {
+        cudaMemsetAsync(err, 0, sizeof(int), stream);
+        rc = set_error(ZM_ERR_TIMEOUT, "a bounded device-side wait gave up (status word set)");
+    }
+    return rc;
+}
 
 // ---- hooks used by zm_api.cu for an FP32C context (a batch of one) ---------------------------
 
@@ -363,8 +404,12 @@ void batch_bind(Batch *b, cudaStream_t s, Prof *p)
     b->prof = p;
 }
 int batch_derivative(Batch *b, int yin) { return b->derivative(yin, b->stream); }
-int batch_vorticity_rate(Batch *b, int yin) { return b->vorticity(yin, 0, 0, 0, 0, 0, b->stream); }
-int batch_step(Batch *b, double dt, int nsteps) { return b->step(dt, nsteps); }
+int batch_vorticity_rate(Batch *b, int yin) { return b->vorticity(yin, 0, 0, 0, 0, b->stream); }
+int batch_step(Batch *b, double dt, int nsteps)
+{
+    int rc = b->set_dt(dt);
+    return rc ? rc : b->step(nsteps, true);
+}
 int batch_status(Batch *b) { return b->status(); }
 
 }  // namespace zm
@@ -379,7 +424,7 @@ struct zm_batch {
 
 static bool batch_index_ok(zm_batch *bt, int32_t index)
 {
-    return bt && index >= 0 && index < bt->b.count;
+    return bt && index >= 0 && index < (int32_t)bt->b.h.size();
 }
 
 static bool dev_ptr(const void *p)
@@ -465,7 +510,7 @@ int zm_batch_velocity(zm_batch *bt)
 {
     if (!bt) return set_error(ZM_ERR_INVALID, "zm_batch_velocity: null batch");
     int rc = bt->b.derivative(0, bt->b.stream);
-    if (!rc) rc = bt->b.vorticity(0, 0, 0, 0, 0, 0, bt->b.stream);
+    if (!rc) rc = bt->b.vorticity(0, 0, 0, 0, 0, bt->b.stream);
     return rc;
 }
 
@@ -485,7 +530,8 @@ int zm_batch_get_velocity(zm_batch *bt, int32_t index, double *u, double *wdot)
 int zm_batch_step(zm_batch *bt, double dt, int32_t nsteps)
 {
     if (!bt || !std::isfinite(dt) || nsteps < 0) return set_error(ZM_ERR_INVALID, "zm_batch_step: bad arguments");
-    return bt->b.step(dt, nsteps);
+    int rc = bt->b.set_dt(dt);
+    return rc ? rc : bt->b.step(nsteps, true);
 }
 
 int zm_batch_sync(zm_batch *bt)

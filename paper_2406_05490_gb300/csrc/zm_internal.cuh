@@ -72,6 +72,7 @@ struct Inst {
     Geom geom;
     Tiling tiling;
     double atwood, g, mu, delta;
+    double dt;                  // RK3 step of this interface
     int block0;                 // first 256-thread block of this interface in the point kernels
     int chunk, nchunks;         // source tiles per Birkhoff-Rott work item; items per target tile
     long long item0;            // first Birkhoff-Rott work item of this interface

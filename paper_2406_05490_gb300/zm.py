@@ -45,6 +45,15 @@ class zm_mesh(ctypes.Structure):
                 ("L2", ctypes.c_double), ("periodic", ctypes.c_int32)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("iterations", "steps", "pairs", "completed", "failed",
+                                               "queued", "running", "peak_running", "bytes_in_use",
+                                               "peak_bytes")] + [("busy_s", ctypes.c_double)]
+
+
+ZM_REQ_QUEUED, ZM_REQ_RUNNING, ZM_REQ_DONE, ZM_REQ_FAILED = 0, 1, 2, 3
+
+
 class zm_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * ZM_K_COUNT), ("launches", ctypes.c_int64 * ZM_K_COUNT),
                 ("pairs", ctypes.c_int64)]
@@ -102,6 +111,16 @@ def load():
             "zm_batch_set_profiling": (I, [VP, I]),
             "zm_batch_get_profile": (I, [VP, ctypes.POINTER(zm_profile)]),
             "zm_batch_destroy": (None, [VP]),
+            "zm_server_create": (I, [ctypes.c_size_t, ctypes.c_int32, D, D, ctypes.POINTER(VP)]),
+            "zm_server_submit": (I, [VP, ctypes.POINTER(zm_mesh), D, D, D, ctypes.c_int32, VP, VP,
+                                     ctypes.POINTER(ctypes.c_int64)]),
+            "zm_server_poll": (I, [VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]),
+            "zm_server_request_bytes": (I, [ctypes.POINTER(zm_mesh), ctypes.POINTER(ctypes.c_size_t)]),
+            "zm_server_wait": (I, [VP, ctypes.c_int64, D]),
+            "zm_server_result": (I, [VP, ctypes.c_int64, VP, VP, ctypes.POINTER(D), ctypes.POINTER(D)]),
+            "zm_server_cancel": (I, [VP, ctypes.c_int64]),
+            "zm_server_get_stats": (I, [VP, ctypes.POINTER(ServerStats)]),
+            "zm_server_destroy": (None, [VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -288,6 +307,64 @@ def zm_batch_get_profile(h):
 def zm_batch_destroy(h):
     if h:
         load().zm_batch_destroy(h)
+
+
+def zm_server_create(mem_budget_bytes, max_slots, g=1.0, mu=0.0):
+    h = VP()
+    _check(load().zm_server_create(int(mem_budget_bytes), int(max_slots), float(g), float(mu),
+                                   ctypes.byref(h)))
+    return h
+
+
+def zm_server_submit(h, n1, n2, z, w, atwood, delta, dt, nsteps, L1=1.0, L2=1.0, periodic=True):
+    m = zm_mesh(int(n1), int(n2), float(L1), float(L2), int(bool(periodic)))
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    rid = ctypes.c_int64()
+    _check(load().zm_server_submit(h, ctypes.byref(m), float(atwood), float(delta), float(dt),
+                                   int(nsteps), ptr(z), ptr(w), ctypes.byref(rid)))
+    return rid.value
+
+
+def zm_server_request_bytes(n1, n2, L1=1.0, L2=1.0, periodic=True):
+    m = zm_mesh(int(n1), int(n2), float(L1), float(L2), int(bool(periodic)))
+    b = ctypes.c_size_t()
+    _check(load().zm_server_request_bytes(ctypes.byref(m), ctypes.byref(b)))
+    return b.value
+
+
+def zm_server_poll(h, rid):
+    st = ctypes.c_int32()
+    _check(load().zm_server_poll(h, int(rid), ctypes.byref(st)))
+    return st.value
+
+
+def zm_server_wait(h, rid, timeout_s=-1.0):
+    return load().zm_server_wait(h, int(rid), float(timeout_s))
+
+
+def zm_server_result(h, rid, N):
+    """(status, z, w, latency_s, queue_s) of a finished request; releases it."""
+    z = np.empty((3, N))
+    w = np.empty((2, N))
+    lat, q = ctypes.c_double(), ctypes.c_double()
+    st = load().zm_server_result(h, int(rid), ptr(z), ptr(w), ctypes.byref(lat), ctypes.byref(q))
+    return st, z, w, lat.value, q.value
+
+
+def zm_server_cancel(h, rid):
+    _check(load().zm_server_cancel(h, int(rid)))
+
+
+def zm_server_get_stats(h):
+    s = ServerStats()
+    _check(load().zm_server_get_stats(h, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in s._fields_}
+
+
+def zm_server_destroy(h):
+    if h:
+        load().zm_server_destroy(h)
 
 
 # ---- a small convenience wrapper -------------------------------------------------------------

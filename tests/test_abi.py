@@ -46,3 +46,18 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(zm, "lib_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(zm.ZMError):
         zm.load()
+
+
+def test_binding_resolves_every_entry_point():
+    """The ctypes binding declares a signature for every exported entry point it wraps, and
+    every name it wraps is declared in include/zm.h (no compute call is made)."""
+    from paper_2406_05490_gb300 import build, zm
+    build.build()
+    zm._lib = None
+    lib = zm.load()
+    declared = set(declared_functions())
+    import inspect
+    for name in dir(zm):
+        if name.startswith("zm_") and inspect.isfunction(getattr(zm, name)):
+            assert name in declared, name
+            assert hasattr(lib, name)

@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / low-order / 32^2 side runs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the side runs (FP64, low order, 32^2, batch, serving)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving runs")
     return ap.parse_args()
 
 
@@ -230,6 +231,150 @@ def timed_steps(model, zm, torch, steps, warmup, flush, profile=True):
     return ms, prof
 
 
+def bench_batched(zm, torch, inputs, flush, steps=10, warmup=2, count=64):
+    """64 periodic interfaces, sides log-uniform in [64, 384] (seed 0), 4 modes, A ~ U[0.2, 0.8],
+    FP32C, one graph-replayed RK3 step per timed step; beside it the same interfaces solved one at
+    a time (FP32C contexts) and the plain per-instance FP64 form on a sample of them."""
+    insts = inputs.ragged_batch(count=count, lo=64, hi=384, n_modes=4, seed=0)
+    meshes = [(r.n, r.n, 1.0, 1.0, True) for r in insts]
+    h = zm.zm_batch_create(meshes, [r.atwood for r in insts], g=1.0, delta=[0.1 / r.n for r in insts])
+    stream = torch.cuda.current_stream()
+    zm.zm_batch_set_stream(h, stream.cuda_stream)
+    for k, r in enumerate(insts):
+        zm.zm_batch_set_state(h, k, r.z, r.w)
+    info = zm.zm_batch_info(h)
+    zm.zm_batch_step(h, 1e-3, warmup)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        zm.zm_batch_step(h, 1e-3, 1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    zm.zm_batch_destroy(h)
+    pairs_step = 3 * info["pairs_per_eval"]
+    out = {"interfaces": count, "sides": [int(r.n) for r in insts], "points": info["points"],
+           "pairs_per_step": pairs_step, "work_items": info["work_items"], "ctas": info["ctas"],
+           "steps": steps, "ms_per_step": ms / steps,
+           "gpairs_per_s": pairs_step * steps / (ms * 1e-3) / 1e9}
+    # the same interfaces one at a time (FP32C contexts, one step each, L2 flushed between)
+    models = []
+    for r in insts:
+        m = zm.ZModel(r.n, periodic=True, atwood=r.atwood, g=1.0, delta=0.1 / r.n, fp32c=True,
+                      stream=stream.cuda_stream)
+        m.set_state(r.z, r.w)
+        m.step(1e-3, 1)
+        models.append(m)
+    torch.cuda.synchronize()
+    t_ms = 0.0
+    for m in models:
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.step(1e-3, 1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_ms += a.elapsed_time(b)
+    for m in models:
+        m.close()
+    out["one_at_a_time_fp32c_gpairs_per_s"] = pairs_step / (t_ms * 1e-3) / 1e9
+    # plain per-instance FP64 form on a sample (the smallest, a median and the largest side)
+    order = sorted(range(count), key=lambda k: insts[k].n)
+    sample = [order[0], order[count // 2], order[-1]]
+    f_pairs, f_ms = 0, 0.0
+    for k in sample:
+        r = insts[k]
+        m = zm.ZModel(r.n, periodic=True, atwood=r.atwood, g=1.0, delta=0.1 / r.n, fp32c=False,
+                      stream=stream.cuda_stream)
+        m.set_state(r.z, r.w)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.step(1e-3, 1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        f_ms += a.elapsed_time(b)
+        f_pairs += 3 * r.n ** 4
+        m.close()
+    out["fp64_per_instance_gpairs_per_s"] = f_pairs / (f_ms * 1e-3) / 1e9
+    out["fp64_per_instance_sample_sides"] = [int(insts[k].n) for k in sample]
+    out["speedup_vs_fp64_per_instance"] = out["gpairs_per_s"] / out["fp64_per_instance_gpairs_per_s"]
+    return out
+
+
+def serve_trace(zm, trace, budget, slots, dt=1e-3):
+    """Replay a trace through the continuous-batching server; latencies from submission."""
+    srv = zm.zm_server_create(budget, slots, g=1.0)
+    t0 = time.perf_counter()
+    ids = []
+    for r in trace:
+        while time.perf_counter() - t0 < r.arrival_s:
+            time.sleep(min(0.001, max(0.0, r.arrival_s - (time.perf_counter() - t0))))
+        ids.append(zm.zm_server_submit(srv, r.n, r.n, r.z, r.w, r.atwood, 0.1 / r.n, dt, r.nsteps))
+    lat, bad = [], 0
+    for r, rid in zip(trace, ids):
+        st = zm.zm_server_wait(srv, rid, 600.0)
+        st, _, _, l, _ = zm.zm_server_result(srv, rid, r.n * r.n)
+        bad += st != zm.ZM_OK
+        lat.append(l)
+    span = time.perf_counter() - t0
+    stats = zm.zm_server_get_stats(srv)
+    zm.zm_server_destroy(srv)
+    import numpy as np
+    lat = np.array(lat)
+    return {"requests": len(trace), "failed": int(bad), "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mean_ms": 1e3 * float(lat.mean()),
+            "makespan_s": span, "gpairs_per_s": stats["pairs"] / span / 1e9,
+            "gpu_busy_frac": stats["busy_s"] / span, "peak_resident": stats["peak_running"],
+            "peak_bytes": stats["peak_bytes"], "iterations": stats["iterations"]}
+
+
+def fp64_sequential_trace(zm, trace, dt=1e-3):
+    """The plain per-instance FP64 form as a server: one request at a time in arrival order,
+    each on its own FP64 context; latency = completion - arrival."""
+    import numpy as np
+    t0 = time.perf_counter()
+    lat, pairs = [], 0
+    for r in trace:
+        while time.perf_counter() - t0 < r.arrival_s:
+            time.sleep(0.0005)
+        m = zm.ZModel(r.n, periodic=True, atwood=r.atwood, g=1.0, delta=0.1 / r.n, fp32c=False)
+        m.set_state(r.z, r.w)
+        m.step(dt, r.nsteps)
+        m.get_state()
+        m.close()
+        lat.append(time.perf_counter() - t0 - r.arrival_s)
+        pairs += 3 * r.nsteps * r.n ** 4
+    span = time.perf_counter() - t0
+    lat = np.array(lat)
+    return {"requests": len(trace), "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "makespan_s": span,
+            "gpairs_per_s": pairs / span / 1e9}
+
+
+def bench_serving(zm, inputs, count=64, budget=16 << 30, slots=64):
+    """Poisson arrivals at 200/s, sides log-uniform in [32, 512], 20 RK3 steps each (FP32C);
+    then the same kind of trace at about 70% of the measured capacity; then a reduced trace
+    (sides [32, 96], 5 steps) served both by the server and by the plain per-instance FP64
+    form, for a like-for-like comparison."""
+    full = inputs.poisson_trace(count=count, rate_hz=200.0, lo=32, hi=512, nsteps=20, seed=0)
+    out = {"offered": serve_trace(zm, full, budget, slots)}
+    out["offered"]["rate_hz"] = 200.0
+    mean_pairs = sum(3 * r.nsteps * r.n ** 4 for r in full) / len(full)
+    cap = out["offered"]["gpairs_per_s"] * 1e9 / mean_pairs
+    rate70 = max(0.7 * cap, 0.1)
+    n70 = max(8, count // 2)
+    t70 = inputs.poisson_trace(count=n70, rate_hz=rate70, lo=32, hi=512, nsteps=20, seed=1)
+    out["at_70pct_capacity"] = serve_trace(zm, t70, budget, slots)
+    out["at_70pct_capacity"]["rate_hz"] = rate70
+    small = inputs.poisson_trace(count=16, rate_hz=200.0, lo=32, hi=96, nsteps=5, seed=2)
+    out["reduced_trace"] = {"server_fp32c": serve_trace(zm, small, budget, slots),
+                            "fp64_per_instance_sequential": fp64_sequential_trace(zm, small)}
+    return out
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -325,6 +470,9 @@ def run_gb300(args):
         ms1, _ = timed_steps(ms_, zm, torch, k1, 3, flush, profile=False)
         ms_.close()
         extras["single_mode_32_fp64"] = {"steps_per_s": k1 / (ms1 * 1e-3), "ms_per_step": ms1 / k1}
+        extras["batched_64"] = bench_batched(zm, torch, inputs, flush)
+        if not args.no_serve:
+            extras["serving"] = bench_serving(zm, inputs)
 
     cpu = None
     if rank == 0 and ws == 1:

@@ -101,6 +101,10 @@ int zm_velocity(zm_ctx *ctx, const double *z, const double *w, double *u, double
  * per step, paper Sec. 3.1 TimeIntegrator).  Asynchronous on the context's stream. */
 int zm_step(zm_ctx *ctx, double dt, int nsteps);
 
+/* Autotune the work decomposition of an FP32C high-order context (see zm_batch_autotune; the
+ * resident state is used, so set it first).  Other contexts have nothing to tune: *chosen = 0. */
+int zm_autotune(zm_ctx *ctx, const char *cache_path, int32_t *chosen);
+
 /* Wait for the context's stream; reports ZM_ERR_TIMEOUT / ZM_ERR_CUDA raised by its kernels. */
 int zm_sync(zm_ctx *ctx);
 
@@ -172,6 +176,13 @@ int zm_batch_step(zm_batch *b, double dt, int32_t nsteps);
 int zm_batch_sync(zm_batch *b);
 /* Tuning: source tiles per all-pairs work item (0 = default by size); results do not change. */
 int zm_batch_set_chunk(zm_batch *b, int32_t chunk);
+/* Autotuner: times work-item sizes 1, 2, 4, ... 32 source tiles on the resident states (one
+ * full derivative evaluation each, twice, CUDA events), keeps the fastest and returns it in
+ * *chosen (and its time per evaluation in *best_ms, or -1 if the choice came from a cache).
+ * Choices are remembered per (GPU model, SM count, occupancy, size buckets) for the process
+ * and, if cache_path is not NULL, appended to / read from that text file.  Results do not
+ * depend on the choice (exact fixed-point accumulation); synchronous. */
+int zm_batch_autotune(zm_batch *b, const char *cache_path, int32_t *chosen, float *best_ms);
 /* Totals: mesh points, pair interactions per evaluation, work items, persistent CTAs. */
 int zm_batch_info(zm_batch *b, int64_t *points, int64_t *pairs_per_eval, int64_t *work_items,
                   int32_t *ctas);

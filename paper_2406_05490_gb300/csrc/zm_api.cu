@@ -91,6 +91,7 @@ int batch_derivative(Batch *b, int yin);
 int batch_vorticity_rate(Batch *b, int yin);
 int batch_step(Batch *b, double dt, int nsteps);
 int batch_status(Batch *b);
+int batch_autotune(Batch *b, const char *path, int *chosen, float *ms);
 
 static int stage_index(zm_ctx *c, const double *y) { return y == c->y0 ? 0 : (y == c->ya ? 1 : 2); }
 
@@ -188,6 +189,8 @@ void zm_destroy(zm_ctx *c)
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     prof_release(c->prof);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap) cudaStreamDestroy(c->cap);
     if (c->batch) {  // state buffers belong to the batch
         batch_delete(c->batch);
         c->batch = nullptr;
@@ -377,27 +380,83 @@ int zm_velocity(zm_ctx *c, const double *z, const double *w, double *u, double *
     return rc;
 }
 
+// One SSP-RK3 step (Shu-Osher): stage s writes ca[s] * y0 + cb[s] * (y_s + dt L(y_s)).
+static int rk3_step_launches(zm_ctx *c, double dt)
+{
+    static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    const double *yin[3] = {c->y0, c->ya, c->yb};
+    double *yout[3] = {c->ya, c->yb, c->y0};
+    for (int st = 0; st < 3; ++st) {
+        int rc = derivative(c, yin[st]);
+        if (!rc) rc = launch_vorticity(c, yin[st], nullptr, c->y0, yout[st], dt, ca[st], cb[st], 1);
+        if (rc) return rc;
+    }
+    return ZM_OK;
+}
+
+// Launch and pair counts of one captured step (what each replay adds to the counters).
+static zm_profile step_counts(const zm_ctx *c)
+{
+    zm_profile d{};
+    d.launches[ZM_K_GEOMETRY] = 3;
+    d.launches[ZM_K_VORT] = 3;
+    if (c->order == ZM_ORDER_LOW) {
+        d.launches[ZM_K_FFT] = 9;
+    } else {
+        d.launches[ZM_K_BR] = 3;
+        d.launches[ZM_K_REDUCE] = 3;
+        d.pairs = 3LL * c->geom.N * c->geom.N;
+    }
+    return d;
+}
+
 int zm_step(zm_ctx *c, double dt, int nsteps)
 {
     if (!c) return set_error(ZM_ERR_INVALID, "zm_step: null context");
     if (!std::isfinite(dt) || nsteps < 0)
         return set_error(ZM_ERR_INVALID, "zm_step: dt must be finite and nsteps >= 0");
-    // SSP-RK3 (Shu-Osher): stage s writes ca[s] * y0 + cb[s] * (y_s + dt L(y_s))
     if (c->batch) {
         batch_bind(c->batch, c->stream, &c->prof);
         return batch_step(c->batch, dt, nsteps);
     }
-    static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
-    static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
-    for (int s = 0; s < nsteps; ++s) {
-        const double *yin[3] = {c->y0, c->ya, c->yb};
-        double *yout[3] = {c->ya, c->yb, c->y0};
-        for (int st = 0; st < 3; ++st) {
-            int rc = derivative(c, yin[st]);
-            if (!rc) rc = launch_vorticity(c, yin[st], nullptr, c->y0, yout[st], dt, ca[st], cb[st], 1);
+    if (nsteps == 0) return ZM_OK;
+    if (c->prof.on) {  // event timing needs plain launches
+        for (int s = 0; s < nsteps; ++s) {
+            int rc = rk3_step_launches(c, dt);
             if (rc) return rc;
         }
+        return ZM_OK;
     }
+    if (!c->gexec || c->gdt != dt) {
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+        if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+            return set_error(ZM_ERR_CUDA, "zm_step: stream creation failed");
+        cudaStream_t user = c->stream;
+        c->stream = c->cap;
+        zm_profile before = c->prof.acc;
+        cudaGraph_t graph = nullptr;
+        int rc = cuda_check(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "zm_step capture");
+        if (!rc) {
+            rc = rk3_step_launches(c, dt);
+            cudaError_t e = cudaStreamEndCapture(c->cap, &graph);
+            if (!rc) rc = cuda_check(e, "zm_step capture end");
+        }
+        c->stream = user;
+        c->prof.acc = before;  // the capture itself launched nothing
+        if (!rc) rc = cuda_check(cudaGraphInstantiate(&c->gexec, graph, 0), "zm_step graph instantiate");
+        if (graph) cudaGraphDestroy(graph);
+        if (rc) return rc;
+        c->gdt = dt;
+        c->step_launches = step_counts(c);
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        int rc = cuda_check(cudaGraphLaunch(c->gexec, c->stream), "zm_step graph launch");
+        if (rc) return rc;
+    }
+    for (int k = 0; k < ZM_K_COUNT; ++k) c->prof.acc.launches[k] += (int64_t)nsteps * c->step_launches.launches[k];
+    c->prof.acc.pairs += (int64_t)nsteps * c->step_launches.pairs;
     return ZM_OK;
 }
 
@@ -410,6 +469,20 @@ int zm_check_finite(zm_ctx *c)
                              "finite flag read");
     if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream), "zm_check_finite");
     if (!rc && h) rc = set_error(ZM_ERR_NONFINITE, "zm_check_finite: state holds NaN or Inf");
+    return rc;
+}
+
+int zm_autotune(zm_ctx *c, const char *cache_path, int32_t *chosen)
+{
+    if (!c) return set_error(ZM_ERR_INVALID, "zm_autotune: null context");
+    if (!c->batch) {  // only the FP32C all-pairs kernel has a tunable work decomposition
+        if (chosen) *chosen = 0;
+        return ZM_OK;
+    }
+    batch_bind(c->batch, c->stream, &c->prof);
+    int ch = 0;
+    int rc = batch_autotune(c->batch, cache_path, &ch, nullptr);
+    if (chosen) *chosen = ch;
     return rc;
 }
 

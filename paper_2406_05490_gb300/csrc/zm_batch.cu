@@ -7,7 +7,10 @@
 // interface; batching many interfaces on one GPU has none.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -264,6 +267,124 @@ int Batch::set_chunk(int chunk)
     return plan();
 }
 
+// ---- autotuner ------------------------------------------------------------------------------
+
+namespace {
+std::mutex g_tune_mutex;
+std::map<std::string, int> g_tune_memo;  // key -> chosen work-item size, for this process
+
+std::string tune_key(const Batch &b)
+{
+    cudaDeviceProp prop;
+    std::memset(&prop, 0, sizeof(prop));
+    cudaGetDeviceProperties(&prop, b.device);
+    std::string name = prop.name;
+    for (auto &ch : name)
+        if (ch == ' ' || ch == '|') ch = '_';
+    long double pairs = 0;
+    int maxtiles = 0;
+    for (auto &I : b.h) {
+        pairs += (long double)I.geom.N * I.geom.N;
+        maxtiles = std::max(maxtiles, I.tiling.ntiles);
+    }
+    const int pb = (int)std::floor(std::log2((double)pairs + 1.0));
+    const int ib = (int)std::floor(std::log2((double)b.h.size()));
+    const int tb = (int)std::floor(std::log2((double)maxtiles + 1.0));
+    return name + "|sm" + std::to_string(b.sms) + "|occ" + std::to_string(b.occ) + "|n2^" +
+           std::to_string(ib) + "|pairs2^" + std::to_string(pb) + "|tiles2^" + std::to_string(tb);
+}
+
+bool cache_lookup(const char *path, const std::string &key, int *chunk)
+{
+    if (!path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char k[512];
+    int c = 0;
+    float ms = 0;
+    bool found = false;
+    while (std::fscanf(f, "%511s %d %f", k, &c, &ms) == 3)
+        if (key == k) {  // the last entry for a key wins
+            *chunk = c;
+            found = true;
+        }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const char *path, const std::string &key, int chunk, float ms)
+{
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %.4f\n", key.c_str(), chunk, ms);
+    std::fclose(f);
+}
+}  // namespace
+
+int Batch::autotune(const char *cache_path, int *chosen, float *best_ms)
+{
+    if (h.empty()) return ZM_OK;
+    const std::string key = tune_key(*this);
+    int c = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_memo.find(key);
+        if (it != g_tune_memo.end()) c = it->second;
+    }
+    if (c <= 0 && cache_lookup(cache_path, key, &c)) {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_memo[key] = c;
+    }
+    if (c > 0) {
+        if (chosen) *chosen = c;
+        if (best_ms) *best_ms = -1.0f;
+        return set_chunk(c);
+    }
+    int maxtiles = 1;
+    for (auto &I : h) maxtiles = std::max(maxtiles, I.tiling.ntiles);
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+        return set_error(ZM_ERR_CUDA, "autotune: event creation failed");
+    Prof *saved = prof;
+    Prof quiet;  // keep the tuning launches out of the caller's counters
+    prof = &quiet;
+    float best = 1e30f;
+    int best_c = 1, rc = ZM_OK;
+    for (int cand = 1; cand <= 32 && cand <= maxtiles; cand *= 2) {
+        rc = set_chunk(cand);
+        if (rc) break;
+        rc = derivative(0, stream);  // warm-up
+        float ms = 0.f, total = 0.f;
+        for (int rep = 0; rep < 2 && !rc; ++rep) {
+            cudaEventRecord(a, stream);
+            rc = derivative(0, stream);
+            cudaEventRecord(b, stream);
+            cudaEventSynchronize(b);
+            cudaEventElapsedTime(&ms, a, b);
+            total += ms;
+        }
+        if (rc) break;
+        if (total < best) {
+            best = total;
+            best_c = cand;
+        }
+    }
+    prof = saved;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    prof_release(quiet);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_memo[key] = best_c;
+    }
+    cache_store(cache_path, key, best_c, best / 2);
+    if (chosen) *chosen = best_c;
+    if (best_ms) *best_ms = best / 2;
+    return set_chunk(best_c);
+}
+
 int Batch::set_dt(double dt)
 {
     bool changed = false;
@@ -411,6 +532,7 @@ int batch_step(Batch *b, double dt, int nsteps)
     return rc ? rc : b->step(nsteps, true);
 }
 int batch_status(Batch *b) { return b->status(); }
+int batch_autotune(Batch *b, const char *path, int *chosen, float *ms) { return b->autotune(path, chosen, ms); }
 
 }  // namespace zm
 
@@ -544,6 +666,15 @@ int zm_batch_set_chunk(zm_batch *bt, int32_t chunk)
 {
     if (!bt || chunk < 0) return set_error(ZM_ERR_INVALID, "zm_batch_set_chunk: bad arguments");
     return bt->b.set_chunk(chunk);
+}
+
+int zm_batch_autotune(zm_batch *bt, const char *cache_path, int32_t *chosen, float *best_ms)
+{
+    if (!bt) return set_error(ZM_ERR_INVALID, "zm_batch_autotune: null batch");
+    int c = 0;
+    int rc = bt->b.autotune(cache_path, &c, best_ms);
+    if (chosen) *chosen = c;
+    return rc;
 }
 
 int zm_batch_info(zm_batch *bt, int64_t *points, int64_t *pairs_per_eval, int64_t *work_items,

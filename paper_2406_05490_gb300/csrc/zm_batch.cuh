@@ -43,6 +43,8 @@ public:
              const double *delta);  // fixed batch owning its slabs
     int plan();                     // (re)build launch plan and descriptors for h
     int set_chunk(int chunk);
+    // time candidate work-item sizes on the resident states, keep the fastest
+    int autotune(const char *cache_path, int *chosen, float *best_ms);
     int set_dt(double dt);          // all members
     void drop_graph();
 

@@ -30,15 +30,25 @@ constexpr int kTile1 = 16, kTile2 = 16;  // source tile: 16 x 16 mesh patch, 256
 template <int kTpb, int kR, int kTs>
 __global__ void __launch_bounds__(kTpb)
     br64_kernel(int N, const double *__restrict__ z, const double *__restrict__ src, int ntiles,
-                int tiles_per_split, double d2, double *__restrict__ part, int *err)
+                int tiles_per_split, int qsplit, double d2, double *__restrict__ part, int *err)
 {
     constexpr uint32_t kBytes = kRec64 * kTs * sizeof(double);
     __shared__ __align__(128) double sh[2][kRec64 * kTs];
     __shared__ __align__(8) uint64_t bar[2];
 
     const int tid = threadIdx.x;
-    const int t0 = blockIdx.y * tiles_per_split;
-    const int nt = max(0, min(ntiles, t0 + tiles_per_split) - t0);
+    // split blockIdx.y: a range of whole tiles, or (qsplit > 1, small meshes) one
+    // 1/qsplit part of one tile's sources
+    int t0, nt, j0 = 0, j1 = kTs;
+    if (qsplit > 1) {
+        t0 = blockIdx.y / qsplit;
+        nt = 1;
+        j0 = (blockIdx.y - t0 * qsplit) * (kTs / qsplit);
+        j1 = j0 + kTs / qsplit;
+    } else {
+        t0 = blockIdx.y * tiles_per_split;
+        nt = max(0, min(ntiles, t0 + tiles_per_split) - t0);
+    }
 
     double tx[kR], ty[kR], tz[kR], ax[kR], ay[kR], az[kR];
 #pragma unroll
@@ -68,7 +78,7 @@ __global__ void __launch_bounds__(kTpb)
         if (ok) {
             const double *s = sh[b];
 #pragma unroll 2
-            for (int jj = 0; jj < kTs; ++jj) {
+            for (int jj = j0; jj < j1; ++jj) {
                 const double sx = s[jj], sy = s[kTs + jj], sz = s[2 * kTs + jj];
                 const double gx = s[3 * kTs + jj], gy = s[4 * kTs + jj], gz = s[5 * kTs + jj];
 #pragma unroll
@@ -116,6 +126,7 @@ __global__ void __launch_bounds__(kTpb)
 }
 
 constexpr int kTpb64 = 128, kR64 = 2;
+constexpr int kTpb64s = 32;  // small meshes: one warp per target block
 
 }  // namespace
 
@@ -136,10 +147,21 @@ BrPlan plan_br(const Geom &g, const Tiling &t, int sm_count)
     BrPlan p;
     p.tpb = kTpb64;
     p.r = kR64;
-    const int per_cta = p.tpb * p.r;
-    p.ntb = (g.N + per_cta - 1) / per_cta;
-    // aim for about four resident CTAs per SM over the whole grid
-    const int want = 4 * sm_count;
+    p.qsplit = 1;
+    const int want = 4 * sm_count;  // about four resident CTAs per SM over the grid
+    p.ntb = (g.N + p.tpb * p.r - 1) / (p.tpb * p.r);
+    if ((long long)p.ntb * t.ntiles < want) {
+        // small mesh: one-warp target blocks and sources split below a tile
+        p.tpb = kTpb64s;
+        p.ntb = (g.N + p.tpb * p.r - 1) / (p.tpb * p.r);
+        p.qsplit = 1;
+        while (p.qsplit < 4 && (long long)p.ntb * t.ntiles * p.qsplit < want) p.qsplit *= 2;
+        if (p.qsplit > 1) {
+            p.tiles_per_split = 1;
+            p.nsplit = t.ntiles * p.qsplit;
+            return p;
+        }
+    }
     int ns = (want + p.ntb - 1) / p.ntb;
     ns = std::max(1, std::min(ns, t.ntiles));
     p.tiles_per_split = (t.ntiles + ns - 1) / ns;
@@ -154,9 +176,14 @@ int launch_br(zm_ctx *c, const double *y)
     dim3 grid(p.ntb, p.nsplit);
     cudaEvent_t ev = nullptr;
     prof_begin(c, ZM_K_BR, &ev);
-    br64_kernel<kTpb64, kR64, kTile1 * kTile2><<<grid, kTpb64, 0, c->stream>>>(
-        g.N, y, static_cast<const double *>(c->src), c->tiling.ntiles, p.tiles_per_split,
-        c->delta * c->delta, c->part, c->err);
+    if (p.tpb == kTpb64s)
+        br64_kernel<kTpb64s, kR64, kTile1 * kTile2><<<grid, kTpb64s, 0, c->stream>>>(
+            g.N, y, static_cast<const double *>(c->src), c->tiling.ntiles, p.tiles_per_split,
+            p.qsplit, c->delta * c->delta, c->part, c->err);
+    else
+        br64_kernel<kTpb64, kR64, kTile1 * kTile2><<<grid, kTpb64, 0, c->stream>>>(
+            g.N, y, static_cast<const double *>(c->src), c->tiling.ntiles, p.tiles_per_split,
+            p.qsplit, c->delta * c->delta, c->part, c->err);
     prof_end(c, ZM_K_BR, ev);
     c->prof.acc.pairs += (int64_t)g.N * (int64_t)g.N;
     return cuda_check(cudaGetLastError(), "Birkhoff-Rott kernel launch");
@@ -290,7 +317,7 @@ extern "C" int zm_br_velocity_noalloc(int32_t n, const double *z, const double *
         n, ntiles, z, gamma, rec, flag);
     const int per_cta = kTpb64 * kR64;
     dim3 grid((n + per_cta - 1) / per_cta, nsplit);
-    br64_kernel<kTpb64, kR64, kNaTs><<<grid, kTpb64, 0, s>>>(n, z, rec, ntiles, tps, delta * delta,
+    br64_kernel<kTpb64, kR64, kNaTs><<<grid, kTpb64, 0, s>>>(n, z, rec, ntiles, tps, 1, delta * delta,
                                                              part, flag);
     na_reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, nsplit, part, u, flag, status);
     return cuda_check(cudaGetLastError(), "zm_br_velocity_noalloc: launch");

@@ -41,6 +41,7 @@ struct BrPlan {
     int r;          // targets per thread (register blocking)
     int nsplit;     // source splits (grid.y); partial sums reduced by a second kernel
     int tiles_per_split;
+    int qsplit;     // > 1: each split is 1/qsplit of one tile's sources (small meshes)
     int ntb;        // target blocks (grid.x)
 };
 
@@ -123,6 +124,12 @@ struct zm_ctx {
 
     zm::Prof prof;
     zm::Batch *batch;  // FP32C high order: the interface lives in a batch of one
+
+    // one RK3 step captured as a CUDA graph (FP64 and low order), replayed by zm_step
+    cudaStream_t cap;
+    cudaGraphExec_t gexec;
+    double gdt;
+    zm_profile step_launches;  // launches and pairs one replayed step adds to the counters
 };
 
 namespace zm {

@@ -106,6 +106,9 @@ def load():
             "zm_batch_step": (I, [VP, D, ctypes.c_int32]),
             "zm_batch_sync": (I, [VP]),
             "zm_batch_set_chunk": (I, [VP, ctypes.c_int32]),
+            "zm_batch_autotune": (I, [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_float)]),
+            "zm_autotune": (I, [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]),
             "zm_batch_info": (I, [VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
             "zm_batch_set_profiling": (I, [VP, I]),
@@ -285,6 +288,21 @@ def zm_batch_sync(h):
 
 def zm_batch_set_chunk(h, chunk):
     _check(load().zm_batch_set_chunk(h, int(chunk)))
+
+
+def zm_batch_autotune(h, cache_path=None):
+    c = ctypes.c_int32()
+    ms = ctypes.c_float()
+    p = cache_path.encode() if cache_path else None
+    _check(load().zm_batch_autotune(h, p, ctypes.byref(c), ctypes.byref(ms)))
+    return c.value, ms.value
+
+
+def zm_autotune(h, cache_path=None):
+    c = ctypes.c_int32()
+    p = cache_path.encode() if cache_path else None
+    _check(load().zm_autotune(h, p, ctypes.byref(c)))
+    return c.value
 
 
 def zm_batch_info(h):

@@ -101,6 +101,27 @@ def test_batch_steps_match_oracle_and_alone(zm):
     zm.zm_batch_destroy(h)
 
 
+def test_batch_autotune(zm, tmp_path):
+    h, delta = make_batch(zm, SPECS)
+    for k, (n1, n2, _, _, s) in enumerate(SPECS):
+        zm.zm_batch_set_state(h, k, *inputs.random_state(n1, n2, seed=s))
+    zm.zm_batch_velocity(h)
+    ref = []
+    for k, (n1, n2, _, _, _) in enumerate(SPECS):
+        u = np.empty((3, n1 * n2))
+        zm.zm_batch_get_velocity(h, k, u, None)
+        ref.append(u)
+    cache = str(tmp_path / "tune.txt")
+    chosen, ms = zm.zm_batch_autotune(h, cache)
+    assert chosen >= 1 and (tmp_path / "tune.txt").read_text().strip()
+    zm.zm_batch_velocity(h)
+    for k, (n1, n2, _, _, _) in enumerate(SPECS):
+        u = np.empty((3, n1 * n2))
+        zm.zm_batch_get_velocity(h, k, u, None)
+        assert np.array_equal(u, ref[k])
+    zm.zm_batch_destroy(h)
+
+
 def test_batch_rejects_bad_arguments(zm):
     with pytest.raises(zm.ZMError) as e:
         zm.zm_batch_create([(4, 4, 1.0, 1.0, True)], [0.5])

@@ -224,3 +224,43 @@ def test_nonfinite_detection(zm):
     model.set_state(z, w)
     assert zm.zm_check_finite(model.h) == zm.ZM_OK
     model.close()
+
+
+@pytest.mark.parametrize("order,fp32c,periodic", [("high", False, False), ("low", False, True),
+                                                   ("high", True, True)])
+def test_graph_replay_equals_plain_launches(zm, order, fp32c, periodic):
+    """zm_step replays one captured CUDA graph per step unless event profiling is on (plain
+    launches); both must give the same bits."""
+    n = 32
+    z0, w0 = inputs.random_state(n, seed=8)
+    od = zm.ZM_ORDER_HIGH if order == "high" else zm.ZM_ORDER_LOW
+    out = []
+    for profiled in (False, True):
+        model = zm.ZModel(n, periodic=periodic, atwood=0.5, g=1.0, order=od, fp32c=fp32c)
+        if profiled:
+            zm.zm_set_profiling(model.h, 1)
+        model.set_state(z0, w0)
+        model.step(1e-3, 3)
+        model.step(2e-3, 2)  # a new dt re-captures the graph
+        out.append(model.get_state())
+        prof = zm.zm_get_profile(model.h)
+        model.close()
+        assert prof["launches"]["geometry"] == 15 and prof["launches"]["vorticity"] == 15
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_autotune_keeps_results(zm):
+    n = 96
+    z, w = inputs.random_state(n, seed=4)
+    model = zm.ZModel(n, periodic=True, fp32c=True)
+    model.set_state(z, w)
+    u0, wd0 = model.velocity()
+    chosen = zm.zm_autotune(model.h)
+    assert chosen in (1, 2, 4, 8, 16, 32)
+    assert zm.zm_autotune(model.h) == chosen  # remembered for the process
+    u1, wd1 = model.velocity()
+    model.close()
+    assert np.array_equal(u0, u1) and np.array_equal(wd0, wd1)
+    m64 = zm.ZModel(n, periodic=True, fp32c=False)
+    assert zm.zm_autotune(m64.h) == 0  # nothing to tune on the FP64 path
+    m64.close()

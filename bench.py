@@ -482,6 +482,17 @@ def run_gb300(args):
         ms1, _ = timed_steps(ms_, zm, torch, k1, 3, flush, profile=False)
         ms_.close()
         extras["single_mode_32_fp64"] = {"steps_per_s": k1 / (ms1 * 1e-3), "ms_per_step": ms1 / k1}
+        # medium order (BR velocity moves the interface, FFT velocity drives the vorticity),
+        # 256^2 periodic, FP32C pair terms
+        mm = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, order=zm.ZM_ORDER_MEDIUM,
+                       fp32c=True)
+        mm.set_state(z0, w0)
+        kmed = 5
+        msm, profm = timed_steps(mm, zm, torch, kmed, 2, flush)
+        mm.close()
+        extras["medium_256_fp32c"] = {"steps_per_s": kmed / (msm * 1e-3), "ms_per_step": msm / kmed,
+                                      "gpairs_per_s": pairs_per_step * kmed / (msm * 1e-3) / 1e9,
+                                      "kernel_ms_per_step": {k: v / kmed for k, v in profm["ms"].items()}}
         extras["batched_64"] = bench_batched(zm, torch, inputs, flush)
         if not args.no_serve:
             extras["serving"] = bench_serving(zm, inputs)

@@ -18,6 +18,8 @@
  *     N = a1 x a2 / |a1 x a2|,  gamma = w1 a2 - w2 a1,
  *     high order:  u_i = -(dx1 dx2 / 4 pi) sum_j (z_i - z_j) x gamma_j / (|z_i - z_j|^2 + delta^2)^(3/2)
  *     low order:   u = -1/2 (R1 w1 + R2 w2) N,   R_l^(k) = -i k_l / |k|  (0 at k = 0, Nyquist)
+ *     medium order: dz/dt = the high-order u, while Phi takes the low-order u (Sec. 2: couples
+ *                  the FFT and far-field solvers; Sec. 6: FFTs for the change in vorticity)
  *     Phi = g z3 + 1/8 (h22 w1^2 - 2 h12 w1 w2 + h11 w2^2) / det + 1/2 |u|^2
  *     dz/dt = u,    dw_l/dt = -2 A D_l Phi + mu (D_1^2 + D_2^2) w_l
  *     SSP-RK3: y1 = y + dt L(y); y2 = 3/4 y + 1/4 (y1 + dt L(y1)); y' = 1/3 y + 2/3 (y2 + dt L(y2)).
@@ -51,8 +53,8 @@ extern "C" {
 #define ZM_ERR_NOMEM (-2)        /* device or host allocation failed                          */
 #define ZM_ERR_CUDA (-3)         /* a CUDA runtime call or kernel launch failed               */
 #define ZM_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up (status word set)      */
-#define ZM_ERR_UNSUPPORTED (-5)  /* valid but not supported: low order on a free-edge mesh,
-                                    FFT side not a power of two, medium order              */
+#define ZM_ERR_UNSUPPORTED (-5)  /* valid but not supported: low/medium order on a free-edge
+                                    mesh, FFT side not a power of two                      */
 #define ZM_ERR_NONFINITE (-6)    /* the state became NaN/Inf (checked by zm_check_finite)    */
 #define ZM_ERR_BUSY (-7)         /* resource budget exhausted (serving admission)            */
 
@@ -77,8 +79,8 @@ typedef struct zm_ctx zm_ctx;
 /* Create a context for one interface on the current CUDA device.  Allocates all device state
  * and workspace (owned by the context until zm_destroy).  delta > 0 is the Birkhoff-Rott core
  * size (high order); mu >= 0 the artificial viscosity; `order` is ZM_ORDER_* | ZM_PREC_*.
- * Returns ZM_ERR_UNSUPPORTED for low order on a free-edge mesh or a non power-of-two side,
- * and for medium order. */
+ * Returns ZM_ERR_UNSUPPORTED for low or medium order on a free-edge mesh or a non power-of-two
+ * side. */
 int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double delta, int order,
               zm_ctx **out);
 

@@ -37,6 +37,7 @@ _lock = threading.Lock()
 _lib = None
 
 ORDER_LOW = 0
+ORDER_MEDIUM = 1
 ORDER_HIGH = 2
 
 

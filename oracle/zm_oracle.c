@@ -26,6 +26,9 @@
  *   Low order (Sec. 2: FFT approximation of the Birkhoff-Rott integral): Riesz transforms
  *       s = R1 w1 + R2 w2,  R_l^(k) = -i k_l / |k|,  k_l = 2 pi m_l / L_l,
  *     multiplier zero at k = 0 and on the Nyquist row and column; u = -1/2 s N.
+ *   Medium order (Sec. 2: couples the FFT and far-field solvers; Sec. 6: uses FFTs for the
+ *     change in vorticity): dz/dt = u from the Birkhoff-Rott sum, while Phi (hence dw/dt) takes
+ *     the low-order velocity.
  *   Vorticity: Phi = g z3 + 1/8 (h22 w1^2 - 2 h12 w1 w2 + h11 w2^2) / det + 1/2 |u|^2,
  *       dw_l/dt = -2 A D_l Phi + mu Lap w_l,     dz/dt = u.
  *   Time integration (Sec. 3.1 "TimeIntegrator": third-order Runge-Kutta, three derivative
@@ -318,20 +321,26 @@ int zmo_derivative(const zmo_mesh *m, const zmo_params *prm, const double *z, co
     double *h = malloc(4 * N * sizeof(double)), *nrm = malloc(3 * N * sizeof(double));
     double *phi = malloc(N * sizeof(double));
     zmo_geometry(m, z, a1, a2, h, nrm);
-    if (prm->order == ZMO_ORDER_HIGH) {
+    double *u_low = NULL;  /* the velocity Phi uses */
+    if (prm->order != ZMO_ORDER_HIGH) {
+        double *s = malloc(N * sizeof(double));
+        u_low = malloc(3 * N * sizeof(double));
+        zmo_riesz_scalar(m, w, s);
+        for (size_t p = 0; p < N; p++)
+            for (int c = 0; c < 3; c++) u_low[c * N + p] = -0.5 * s[p] * nrm[c * N + p];
+        free(s);
+    }
+    if (prm->order != ZMO_ORDER_LOW) {
         double *gamma = malloc(3 * N * sizeof(double));
         zmo_sheet_strength(N, w, a1, a2, gamma);
         double weight = (m->L1 / m->n1) * (m->L2 / m->n2);
         zmo_br_velocity(N, z, N, z, gamma, weight, prm->delta, u);
         free(gamma);
     } else {
-        double *s = malloc(N * sizeof(double));
-        zmo_riesz_scalar(m, w, s);
-        for (size_t p = 0; p < N; p++)
-            for (int c = 0; c < 3; c++) u[c * N + p] = -0.5 * s[p] * nrm[c * N + p];
-        free(s);
+        memcpy(u, u_low, 3 * N * sizeof(double));
     }
-    zmo_phi(N, z, w, h, u, prm->g, phi);
+    zmo_phi(N, z, w, h, u_low ? u_low : u, prm->g, phi);
+    free(u_low);
     if (wdot) zmo_wdot(m, phi, w, prm->atwood, prm->mu, wdot);
     free(a1); free(a2); free(h); free(nrm); free(phi);
     return 0;

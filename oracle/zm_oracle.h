@@ -12,7 +12,7 @@
 extern "C" {
 #endif
 
-enum { ZMO_ORDER_LOW = 0, ZMO_ORDER_HIGH = 2 };
+enum { ZMO_ORDER_LOW = 0, ZMO_ORDER_MEDIUM = 1, ZMO_ORDER_HIGH = 2 };
 
 typedef struct {
     int n1, n2;      /* nodes along alpha1 (slow index) and alpha2 (fast index) */
@@ -22,7 +22,7 @@ typedef struct {
 
 typedef struct {
     double atwood, g, mu, delta;
-    int order;       /* ZMO_ORDER_LOW or ZMO_ORDER_HIGH */
+    int order;       /* ZMO_ORDER_LOW, ZMO_ORDER_MEDIUM or ZMO_ORDER_HIGH */
 } zmo_params;
 
 /* All field arrays are component-major: f[c * n1 * n2 + i * n2 + j]. */

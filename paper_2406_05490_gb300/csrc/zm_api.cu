@@ -91,6 +91,7 @@ int batch_derivative(Batch *b, int yin);
 int batch_vorticity_rate(Batch *b, int yin);
 int batch_step(Batch *b, double dt, int nsteps);
 int batch_status(Batch *b);
+int batch_keep_phi(Batch *b, int on);
 int batch_autotune(Batch *b, const char *path, int *chosen, float *ms);
 
 static int stage_index(zm_ctx *c, const double *y) { return y == c->y0 ? 0 : (y == c->ya ? 1 : 2); }
@@ -102,14 +103,28 @@ int derivative(zm_ctx *c, const double *y)
 {
     if (c->batch) {
         batch_bind(c->batch, c->stream, &c->prof);
+        if (c->order == ZM_ORDER_MEDIUM) {
+            // normals and q, then u and Phi from the FFT velocity; the batched sum then
+            // replaces u and leaves Phi (keep_phi)
+            int rc = launch_geometry(c, y);
+            if (!rc) rc = launch_riesz(c, y);
+            if (rc) return rc;
+        }
         return batch_derivative(c->batch, stage_index(c, y));
     }
     int rc = launch_geometry(c, y);
     if (rc) return rc;
     if (c->order == ZM_ORDER_LOW) return launch_riesz(c, y);
+    if (c->order == ZM_ORDER_MEDIUM) {
+        // Phi from the FFT velocity (written with u, which the BR sum then replaces)
+        rc = launch_riesz(c, y);
+        if (rc) return rc;
+        rc = launch_br(c, y);
+        return rc ? rc : launch_reduce(c, false);
+    }
     rc = launch_br(c, y);
     if (rc) return rc;
-    return launch_reduce(c);
+    return launch_reduce(c, true);
 }
 
 static bool is_device_ptr(const void *p)
@@ -221,15 +236,16 @@ int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double de
         return set_error(ZM_ERR_INVALID, "zm_create: atwood, g must be finite and mu >= 0");
     if (ord == ZM_ORDER_HIGH && !(delta > 0 && std::isfinite(delta)))
         return set_error(ZM_ERR_INVALID, "zm_create: the Birkhoff-Rott core size delta must be > 0");
-    if (ord == ZM_ORDER_MEDIUM)
-        return set_error(ZM_ERR_UNSUPPORTED, "zm_create: medium order is not implemented");
-    if (ord == ZM_ORDER_LOW && !mesh->periodic)
+    const bool fft = (ord == ZM_ORDER_LOW || ord == ZM_ORDER_MEDIUM);
+    if (ord == ZM_ORDER_MEDIUM && !(delta > 0 && std::isfinite(delta)))
+        return set_error(ZM_ERR_INVALID, "zm_create: the Birkhoff-Rott core size delta must be > 0");
+    if (fft && !mesh->periodic)
         return set_error(ZM_ERR_UNSUPPORTED,
-                         "zm_create: low order needs a periodic mesh (periodic FFT solver)");
-    if (ord == ZM_ORDER_LOW && (!pow2(mesh->n1) || !pow2(mesh->n2) || mesh->n1 > 4096 ||
-                                mesh->n2 > 4096 || mesh->n1 < 8 || mesh->n2 < 8))
+                         "zm_create: low and medium order need a periodic mesh (periodic FFT solver)");
+    if (fft && (!pow2(mesh->n1) || !pow2(mesh->n2) || mesh->n1 > 4096 || mesh->n2 > 4096 ||
+                mesh->n1 < 8 || mesh->n2 < 8))
         return set_error(ZM_ERR_UNSUPPORTED,
-                         "zm_create: low order needs power-of-two sides in [8, 4096]");
+                         "zm_create: low and medium order need power-of-two sides in [8, 4096]");
 
     zm_ctx *c = new (std::nothrow) zm_ctx();
     if (!c) return set_error(ZM_ERR_NOMEM, "zm_create: host allocation failed");
@@ -264,10 +280,14 @@ int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double de
         return true;
     };
     bool ok = alloc((void **)&c->err, sizeof(int)) && alloc((void **)&c->flag, sizeof(int));
-    if (ok && ord == ZM_ORDER_HIGH && fp32c) {
+    if (ok && (ord == ZM_ORDER_HIGH || ord == ZM_ORDER_MEDIUM) && fp32c) {
         int rc = ZM_OK;
         c->batch = batch_new_single(mesh, atwood, g, mu, delta, &rc);
         if (!c->batch) {
+            zm_destroy(c);
+            return rc;
+        }
+        if (ord == ZM_ORDER_MEDIUM && (rc = batch_keep_phi(c->batch, 1)) != ZM_OK) {
             zm_destroy(c);
             return rc;
         }
@@ -286,7 +306,7 @@ int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double de
              alloc((void **)&c->u, 3 * N * sizeof(double)) &&
              alloc((void **)&c->phi, N * sizeof(double)) && alloc((void **)&c->q, N * sizeof(double));
     }
-    if (ok && ord == ZM_ORDER_HIGH && !fp32c) {
+    if (ok && (ord == ZM_ORDER_HIGH || ord == ZM_ORDER_MEDIUM) && !fp32c) {
         c->tiling = make_tiling(G);
         const size_t slots = (size_t)c->tiling.ntiles * c->tiling.ts;
         c->plan = plan_br(G, c->tiling, sms);
@@ -296,14 +316,14 @@ int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double de
         // padding slots of edge tiles stay zero for good: zero strength, no contribution
         if (ok) ok = cudaMemset(c->src, 0, c->src_bytes) == cudaSuccess;
     }
-    if (ok && ord == ZM_ORDER_LOW) ok = alloc((void **)&c->nrm, 3 * N * sizeof(double));
+    if (ok && fft) ok = alloc((void **)&c->nrm, 3 * N * sizeof(double));
     if (ok) ok = cudaMemset(c->err, 0, sizeof(int)) == cudaSuccess &&
                  cudaMemset(c->y0, 0, 5 * N * sizeof(double)) == cudaSuccess;
     if (!ok) {
         zm_destroy(c);
         return set_error(ZM_ERR_NOMEM, "zm_create: device allocation failed");
     }
-    if (ord == ZM_ORDER_LOW) {
+    if (fft) {
         int rc = fft_setup(c);
         if (rc) {
             zm_destroy(c);
@@ -403,6 +423,12 @@ static zm_profile step_counts(const zm_ctx *c)
     d.launches[ZM_K_VORT] = 3;
     if (c->order == ZM_ORDER_LOW) {
         d.launches[ZM_K_FFT] = 9;
+    } else if (c->order == ZM_ORDER_MEDIUM) {
+        d.launches[ZM_K_GEOMETRY] = 6;
+        d.launches[ZM_K_FFT] = 9;
+        d.launches[ZM_K_BR] = 3;
+        d.launches[ZM_K_REDUCE] = 3;
+        d.pairs = 3LL * c->geom.N * c->geom.N;
     } else {
         d.launches[ZM_K_BR] = 3;
         d.launches[ZM_K_REDUCE] = 3;
@@ -416,7 +442,7 @@ int zm_step(zm_ctx *c, double dt, int nsteps)
     if (!c) return set_error(ZM_ERR_INVALID, "zm_step: null context");
     if (!std::isfinite(dt) || nsteps < 0)
         return set_error(ZM_ERR_INVALID, "zm_step: dt must be finite and nsteps >= 0");
-    if (c->batch) {
+    if (c->batch && c->order == ZM_ORDER_HIGH) {
         batch_bind(c->batch, c->stream, &c->prof);
         return batch_step(c->batch, dt, nsteps);
     }

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kPtb)
         I.ufix[c * N + p] = 0ull;
         I.u[c * N + p] = s[c];
     }
-    I.phi[p] = I.q[p] + 0.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    if (!I.keep_phi) I.phi[p] = I.q[p] + 0.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
     if (p < I.tiling.ntiles) I.tinfo[p] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (p == 0) *I.gmax = 0u;
 }
@@ -532,6 +532,11 @@ int batch_step(Batch *b, double dt, int nsteps)
     return rc ? rc : b->step(nsteps, true);
 }
 int batch_status(Batch *b) { return b->status(); }
+int batch_keep_phi(Batch *b, int on)
+{
+    for (auto &I : b->h) I.keep_phi = on;
+    return b->plan();
+}
 int batch_autotune(Batch *b, const char *path, int *chosen, float *ms) { return b->autotune(path, chosen, ms); }
 
 }  // namespace zm

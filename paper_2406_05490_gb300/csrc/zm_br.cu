@@ -171,6 +171,7 @@ BrPlan plan_br(const Geom &g, const Tiling &t, int sm_count)
 
 int launch_br(zm_ctx *c, const double *y)
 {
+    if (!y || !c->src || !c->part) return set_error(ZM_ERR_INVALID, "Birkhoff-Rott pass: missing buffer");
     const Geom &g = c->geom;
     const BrPlan &p = c->plan;
     dim3 grid(p.ntb, p.nsplit);

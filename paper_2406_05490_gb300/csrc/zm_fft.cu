@@ -199,6 +199,8 @@ int fft_setup(zm_ctx *c)
 
 int launch_riesz(zm_ctx *c, const double *y)
 {
+    if (!y || !c->fa || !c->fb || !c->tw1 || !c->tw2 || !c->nrm || !c->q || !c->u || !c->phi)
+        return set_error(ZM_ERR_INVALID, "Riesz pass: missing buffer");
     const Geom &g = c->geom;
     const int l1 = ilog2(g.n1), l2 = ilog2(g.n2);
     const int ra = rows_for(g.n2), rb = rows_for(g.n1);

@@ -74,6 +74,7 @@ struct Inst {
     Tiling tiling;
     double atwood, g, mu, delta;
     double dt;                  // RK3 step of this interface
+    int keep_phi;               // medium order: Phi comes from the FFT velocity, not from u
     int block0;                 // first 256-thread block of this interface in the point kernels
     int chunk, nchunks;         // source tiles per Birkhoff-Rott work item; items per target tile
     long long item0;            // first Birkhoff-Rott work item of this interface
@@ -153,8 +154,8 @@ int launch_geometry(zm_ctx *c, const double *y);
 // yout = ca * y0 + cb * (y + dt * L(y)), L = (u, dw/dt).
 int launch_vorticity(zm_ctx *c, const double *y, double *wdot_out, const double *y0, double *yout,
                      double dt, double ca, double cb, int mode);
-// Reduce split partials into u and phi.
-int launch_reduce(zm_ctx *c);
+// Reduce split partials into u and, if write_phi, Phi = q + |u|^2 / 2.
+int launch_reduce(zm_ctx *c, bool write_phi);
 // Set *dev_flag (device int) to 1 if any of y[0..n) is NaN/Inf.
 int check_finite(zm_ctx *c, const double *y, size_t n, int *dev_flag);
 

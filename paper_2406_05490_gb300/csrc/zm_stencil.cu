@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kTpb)
 
 __global__ void __launch_bounds__(kTpb)
     reduce_kernel(int N, int nsplit, const double *__restrict__ part, const double *__restrict__ q,
-                  double *__restrict__ u, double *__restrict__ phi)
+                  double *__restrict__ u, double *__restrict__ phi, int write_phi)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kTpb)
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) u[(size_t)c * N + p] = s[c];
-    phi[p] = q[p] + 0.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    if (write_phi) phi[p] = q[p] + 0.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
 }
 
 template <bool kVisc, int kMode>
@@ -74,28 +74,40 @@ int check_finite(zm_ctx *c, const double *y, size_t n, int *dev_flag)
 
 int launch_geometry(zm_ctx *c, const double *y)
 {
+    // every buffer a launch below writes must exist (a wiring error returns, never faults)
+    if (!y || !c->q || (c->order != ZM_ORDER_HIGH && !c->nrm) ||
+        (c->order != ZM_ORDER_LOW && !c->batch && !c->src))
+        return set_error(ZM_ERR_INVALID, "geometry pass: missing buffer");
     const Geom &g = c->geom;
     const double pref = g.dx1 * g.dx2 / (4.0 * 3.14159265358979323846);
     dim3 grid((g.N + kTpb - 1) / kTpb);
     cudaEvent_t ev = nullptr;
     prof_begin(c, ZM_K_GEOMETRY, &ev);
-    if (c->order == ZM_ORDER_LOW)
+    if (c->order != ZM_ORDER_HIGH)
         geometry_kernel<kGeoLow><<<grid, kTpb, 0, c->stream>>>(g, c->tiling, y, pref, c->g, nullptr,
                                                              c->q, c->nrm);
-    else
+    // FP64 source records (high and medium order); FP32C contexts build theirs in the batch
+    if (c->order != ZM_ORDER_LOW && !c->batch) {
+        if (c->order == ZM_ORDER_MEDIUM) {  // the second geometry pass of a medium-order evaluation
+            prof_end(c, ZM_K_GEOMETRY, ev);
+            prof_begin(c, ZM_K_GEOMETRY, &ev);
+        }
         geometry_kernel<kGeoFp64><<<grid, kTpb, 0, c->stream>>>(g, c->tiling, y, pref, c->g, c->src,
                                                               c->q, nullptr);
+    }
     prof_end(c, ZM_K_GEOMETRY, ev);
     return cuda_check(cudaGetLastError(), "geometry kernel launch");
 }
 
-int launch_reduce(zm_ctx *c)
+int launch_reduce(zm_ctx *c, bool write_phi)
 {
+    if (!c->part || !c->u || !c->phi || !c->q) return set_error(ZM_ERR_INVALID, "reduction: missing buffer");
     const Geom &g = c->geom;
     dim3 grid((g.N + kTpb - 1) / kTpb);
     cudaEvent_t ev = nullptr;
     prof_begin(c, ZM_K_REDUCE, &ev);
-    reduce_kernel<<<grid, kTpb, 0, c->stream>>>(g.N, c->plan.nsplit, c->part, c->q, c->u, c->phi);
+    reduce_kernel<<<grid, kTpb, 0, c->stream>>>(g.N, c->plan.nsplit, c->part, c->q, c->u, c->phi,
+                                                write_phi ? 1 : 0);
     prof_end(c, ZM_K_REDUCE, ev);
     return cuda_check(cudaGetLastError(), "reduce kernel launch");
 }
@@ -103,6 +115,8 @@ int launch_reduce(zm_ctx *c)
 int launch_vorticity(zm_ctx *c, const double *y, double *wdot_out, const double *y0, double *yout,
                      double dt, double ca, double cb, int mode)
 {
+    if (!y || !c->phi || !c->u || (mode == 0 && !wdot_out) || (mode == 1 && (!y0 || !yout)))
+        return set_error(ZM_ERR_INVALID, "vorticity pass: missing buffer");
     const Geom &g = c->geom;
     dim3 grid((g.N + kTpb - 1) / kTpb);
     cudaEvent_t ev = nullptr;

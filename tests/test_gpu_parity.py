@@ -96,6 +96,34 @@ def test_low_order_parity(zm, n1, n2):
     assert eu <= TOL64 and ew <= TOL64
 
 
+@pytest.mark.parametrize("fp32c", [False, True])
+@pytest.mark.parametrize("n1,n2", [(16, 16), (64, 32)])
+def test_medium_order_parity(zm, n1, n2, fp32c):
+    """Medium order: dz/dt from the Birkhoff-Rott sum, Phi from the FFT velocity."""
+    tol = TOL32 if fp32c else TOL64
+    z, w = inputs.random_state(n1, n2, seed=n1 * 3 + n2)
+    delta = 0.1 / max(n1, n2)
+    m = oracle.Mesh(n1, n2, periodic=True)
+    u_ref, wd_ref = oracle.derivative(m, z, w, 0.6, 1.2, 0.01, delta, order=oracle.ORDER_MEDIUM)
+    model = zm.ZModel(n1, n2, periodic=True, atwood=0.6, g=1.2, mu=0.01, delta=delta,
+                      order=zm.ZM_ORDER_MEDIUM, fp32c=fp32c)
+    u, wd = model.velocity(z, w)
+    model.close()
+    eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+    print(f"medium order {n1}x{n2} fp32c={fp32c}: rel L2 u={eu:.3e} wdot={ew:.3e}")
+    assert eu <= tol and ew <= tol
+    # and stepping
+    z0, w0 = inputs.multi_mode(n1, n_modes=4, seed=2, amp=0.02) if n1 == n2 else (z, w)
+    zr, wr = oracle.run(m, z0, w0, 0.6, 1.2, 0.0, delta, 2e-3, 3, order=oracle.ORDER_MEDIUM)
+    model = zm.ZModel(n1, n2, periodic=True, atwood=0.6, g=1.2, delta=delta, order=zm.ZM_ORDER_MEDIUM,
+                      fp32c=fp32c)
+    model.set_state(z0, w0)
+    model.step(2e-3, 3)
+    z1, w1 = model.get_state()
+    model.close()
+    assert rel(z1, zr) <= tol and rel(w1, wr) <= tol
+
+
 def test_low_order_steps(zm):
     n = 64
     z0, w0 = inputs.multi_mode(n, n_modes=8, seed=3, amp=0.02)
@@ -209,7 +237,7 @@ def test_invalid_arguments(zm):
         zm.zm_create(48, 48, periodic=True, order=zm.ZM_ORDER_LOW)
     assert e.value.code == zm.ZM_ERR_UNSUPPORTED
     with pytest.raises(zm.ZMError) as e:
-        zm.zm_create(32, 32, order=zm.ZM_ORDER_MEDIUM)
+        zm.zm_create(32, 32, periodic=False, order=zm.ZM_ORDER_MEDIUM)
     assert e.value.code == zm.ZM_ERR_UNSUPPORTED
 
 

@@ -348,6 +348,20 @@ def test_riesz_gradient_mode_and_curl():
     assert np.all(u[0] == 0.0) and np.all(u[1] == 0.0)
 
 
+def test_medium_order_composition():
+    """Medium order moves the interface with the Birkhoff-Rott velocity and updates the vorticity
+    with the FFT velocity, so its u equals the high-order u and its dw/dt the low-order dw/dt."""
+    n = 32
+    m = oracle.Mesh(n, periodic=True)
+    z, w = inputs.random_state(n, seed=17)
+    args = (0.6, 1.2, 0.01, 0.1 / n)
+    um, wm = oracle.derivative(m, z, w, *args, order=oracle.ORDER_MEDIUM)
+    uh, wh = oracle.derivative(m, z, w, *args, order=oracle.ORDER_HIGH)
+    ul, wl = oracle.derivative(m, z, w, *args, order=oracle.ORDER_LOW)
+    assert np.array_equal(um, uh) and np.array_equal(wm, wl)
+    assert not np.array_equal(uh, ul) and not np.array_equal(wh, wl)
+
+
 # ------------------------------------------------------------------------------------------
 # time integration and the linear Rayleigh-Taylor limit
 # ------------------------------------------------------------------------------------------

@@ -38,6 +38,16 @@ constexpr int kR = 4;     // targets per thread: one 16 x 16 target tile per CTA
 constexpr int kTs = 256;  // sources per tile
 constexpr float kFarFactor = 1.25f;
 
+// compile-time tuning: unroll of the far loop over source pairs, and the minimum resident CTAs
+// per SM the register allocation must allow
+#ifndef ZM_BR32_UNROLL
+#define ZM_BR32_UNROLL 2
+#endif
+#ifndef ZM_BR32_MINB
+#define ZM_BR32_MINB 7
+#endif
+constexpr int kFarUnroll = ZM_BR32_UNROLL;
+
 typedef unsigned long long u64;  // two packed floats (low word first)
 
 __device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
@@ -93,7 +103,7 @@ struct Unit {
     int far;
 };
 
-__global__ void __launch_bounds__(kT, 8)
+__global__ void __launch_bounds__(kT, ZM_BR32_MINB)
     br32_batch_kernel(const Inst *__restrict__ insts, int ninst, long long nitems,
                       unsigned long long *counter, int *err)
 {
@@ -230,7 +240,7 @@ __global__ void __launch_bounds__(kT, 8)
                     ax[r] = ay[r] = az[r] = gxs[r] = gys[r] = gzs[r] = 0ull;
                 }
                 const u64 *s2 = reinterpret_cast<const u64 *>(s);  // row k, sources (2m, 2m+1)
-#pragma unroll 1
+#pragma unroll kFarUnroll
                 for (int m = 0; m < kTs / 2; ++m) {
                     const u64 sx = s2[m], sy = s2[kTs / 2 + m], sz = s2[kTs + m], sa = s2[3 * (kTs / 2) + m];
                     const u64 gx = s2[2 * kTs + m], gy = s2[5 * (kTs / 2) + m], gz = s2[3 * kTs + m];

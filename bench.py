@@ -311,6 +311,37 @@ def bench_batched(zm, torch, inputs, flush, steps=10, warmup=2, count=64):
     return out
 
 
+def bench_cutoff(zm, torch, inputs, n=256, cutoffs=(0.05, 0.1, 0.2, 0.4)):
+    """Accuracy/performance trade-off of the cutoff sum against the exact all-pairs sum (the
+    purpose the paper gives the exact solver, Sec. 3.2.1): one derivative evaluation of the
+    256^2 interface with vorticity per cutoff; time of the all-pairs kernel and relative L2
+    difference of u from the exact sum."""
+    import numpy as np
+    z, _ = inputs.multi_mode(n, n_modes=16, seed=0)
+    _, w = inputs.random_state(n, seed=1)
+    m = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, fp32c=True,
+                  stream=torch.cuda.current_stream().cuda_stream)
+    m.set_state(z, w)
+
+    def one(c):
+        zm.zm_set_cutoff(m.h, c)
+        m.velocity(want_wdot=False)  # warm-up
+        zm.zm_set_profiling(m.h, 1)
+        u = m.velocity(want_wdot=False)
+        p = zm.zm_get_profile(m.h)
+        zm.zm_set_profiling(m.h, 0)
+        return u, p["ms"]["br"] / max(p["launches"]["br"], 1)
+
+    u_ex, t_ex = one(0.0)
+    rows = []
+    for c in cutoffs:
+        u, t = one(c)
+        rows.append({"cutoff": c, "br_ms": t, "speedup": t_ex / t,
+                     "rel_l2_vs_exact": float(np.linalg.norm(u - u_ex) / np.linalg.norm(u_ex))})
+    m.close()
+    return {"n_side": n, "exact_br_ms": t_ex, "cutoffs": rows}
+
+
 def serve_trace(zm, trace, budget, slots, dt=1e-3):
     """Replay a trace through the continuous-batching server; latencies from submission."""
     srv = zm.zm_server_create(budget, slots, g=1.0)
@@ -493,6 +524,7 @@ def run_gb300(args):
         extras["medium_256_fp32c"] = {"steps_per_s": kmed / (msm * 1e-3), "ms_per_step": msm / kmed,
                                       "gpairs_per_s": pairs_per_step * kmed / (msm * 1e-3) / 1e9,
                                       "kernel_ms_per_step": {k: v / kmed for k, v in profm["ms"].items()}}
+        extras["cutoff_tradeoff_256"] = bench_cutoff(zm, torch, inputs)
         extras["batched_64"] = bench_batched(zm, torch, inputs, flush)
         if not args.no_serve:
             extras["serving"] = bench_serving(zm, inputs)

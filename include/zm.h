@@ -103,6 +103,12 @@ int zm_velocity(zm_ctx *ctx, const double *z, const double *w, double *u, double
  * per step, paper Sec. 3.1 TimeIntegrator).  Asynchronous on the context's stream. */
 int zm_step(zm_ctx *ctx, double dt, int nsteps);
 
+/* Cutoff Birkhoff-Rott sum (paper Sec. 3.2.2, CutoffBRSolver): from now on sum only over the
+ * sources within `cutoff` of each target (0 = all sources, the exact sum).  A pair is in iff
+ * |r|^2 <= cutoff^2 with r formed from FP32 hi/lo positions and |r|^2 rounded to FP32.  FP32C
+ * contexts (high or medium order); ZM_ERR_UNSUPPORTED otherwise. */
+int zm_set_cutoff(zm_ctx *ctx, double cutoff);
+
 /* Autotune the work decomposition of an FP32C high-order context (see zm_batch_autotune; the
  * resident state is used, so set it first).  Other contexts have nothing to tune: *chosen = 0. */
 int zm_autotune(zm_ctx *ctx, const char *cache_path, int32_t *chosen);
@@ -185,6 +191,8 @@ int zm_batch_set_chunk(zm_batch *b, int32_t chunk);
  * and, if cache_path is not NULL, appended to / read from that text file.  Results do not
  * depend on the choice (exact fixed-point accumulation); synchronous. */
 int zm_batch_autotune(zm_batch *b, const char *cache_path, int32_t *chosen, float *best_ms);
+/* Cutoff sum (see zm_set_cutoff) for interface `index`, or all interfaces if index = -1. */
+int zm_batch_set_cutoff(zm_batch *b, int32_t index, double cutoff);
 /* Totals: mesh points, pair interactions per evaluation, work items, persistent CTAs. */
 int zm_batch_info(zm_batch *b, int64_t *points, int64_t *pairs_per_eval, int64_t *work_items,
                   int32_t *ctas);

@@ -62,7 +62,7 @@ class _Mesh(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("atwood", ctypes.c_double), ("g", ctypes.c_double), ("mu", ctypes.c_double),
-                ("delta", ctypes.c_double), ("order", ctypes.c_int)]
+                ("delta", ctypes.c_double), ("order", ctypes.c_int), ("cutoff", ctypes.c_double)]
 
 
 _P = ctypes.POINTER(ctypes.c_double)
@@ -83,6 +83,7 @@ def _load():
                 "zmo_geometry": (None, [M, _P, _P, _P, _P, _P]),
                 "zmo_sheet_strength": (None, [sz, _P, _P, _P, _P]),
                 "zmo_br_velocity": (None, [sz, _P, sz, _P, _P, d, d, _P]),
+                "zmo_br_velocity_cutoff": (None, [sz, _P, sz, _P, _P, d, d, d, _P]),
                 "zmo_fft2": (None, [i, i, _P, _P, i]),
                 "zmo_riesz_scalar": (None, [M, _P, _P]),
                 "zmo_phi": (None, [sz, _P, _P, _P, _P, d, _P]),
@@ -126,8 +127,8 @@ class Mesh:
         return _Mesh(self.n1, self.n2, self.L1, self.L2, int(self.periodic))
 
 
-def _params(atwood, g, mu, delta, order):
-    return _Params(float(atwood), float(g), float(mu), float(delta), int(order))
+def _params(atwood, g, mu, delta, order, cutoff=0.0):
+    return _Params(float(atwood), float(g), float(mu), float(delta), int(order), float(cutoff))
 
 
 def diff1(mesh, f, axis, shift=0.0):
@@ -183,6 +184,20 @@ def br_velocity(zt, zs, gamma, weight, delta):
     return u
 
 
+def br_velocity_cutoff(zt, zs, gamma, weight, delta, cutoff):
+    """br_velocity over the sources within `cutoff` of each target (decision in FP32, see
+    zm_oracle.c)."""
+    lib = _load()
+    zt = _arr(zt)
+    zs = _arr(zs)
+    nt, ns = zt.shape[-1], zs.shape[-1]
+    zt, zs, gamma = zt.reshape(3, nt), zs.reshape(3, ns), _arr(gamma, (3, ns))
+    u = np.empty((3, nt))
+    lib.zmo_br_velocity_cutoff(nt, _ptr(zt), ns, _ptr(zs), _ptr(gamma), float(weight), float(delta),
+                               float(cutoff), _ptr(u))
+    return u
+
+
 def fft2(re, im, sign):
     lib = _load()
     re = _arr(re).copy()
@@ -219,20 +234,20 @@ def wdot(mesh, phi_, w, atwood, mu):
     return out
 
 
-def derivative(mesh, z, w, atwood, g, mu, delta, order=ORDER_HIGH):
+def derivative(mesh, z, w, atwood, g, mu, delta, order=ORDER_HIGH, cutoff=0.0):
     """One evaluation L(z, w) = (u, wdot) of the Z-Model derivative."""
     lib = _load()
     z, w = _arr(z, (3, mesh.N)), _arr(w, (2, mesh.N))
     u, wd = np.empty((3, mesh.N)), np.empty((2, mesh.N))
-    m, p = mesh.c(), _params(atwood, g, mu, delta, order)
+    m, p = mesh.c(), _params(atwood, g, mu, delta, order, cutoff)
     lib.zmo_derivative(ctypes.byref(m), ctypes.byref(p), _ptr(z), _ptr(w), _ptr(u), _ptr(wd))
     return u, wd
 
 
-def run(mesh, z, w, atwood, g, mu, delta, dt, nsteps, order=ORDER_HIGH):
+def run(mesh, z, w, atwood, g, mu, delta, dt, nsteps, order=ORDER_HIGH, cutoff=0.0):
     """Advance (z, w) by nsteps SSP-RK3 steps; returns new arrays."""
     lib = _load()
     z, w = _arr(z, (3, mesh.N)).copy(), _arr(w, (2, mesh.N)).copy()
-    m, p = mesh.c(), _params(atwood, g, mu, delta, order)
+    m, p = mesh.c(), _params(atwood, g, mu, delta, order, cutoff)
     lib.zmo_run(ctypes.byref(m), ctypes.byref(p), _ptr(z), _ptr(w), float(dt), int(nsteps))
     return z, w

@@ -26,6 +26,11 @@
  *   Low order (Sec. 2: FFT approximation of the Birkhoff-Rott integral): Riesz transforms
  *       s = R1 w1 + R2 w2,  R_l^(k) = -i k_l / |k|,  k_l = 2 pi m_l / L_l,
  *     multiplier zero at k = 0 and on the Nyquist row and column; u = -1/2 s N.
+ *   Cutoff (Sec. 3.2.2 CutoffBRSolver: only the points within a 3D distance of each point):
+ *     the same sum restricted to |z_i - z_j| <= cutoff.  Whether a pair is in is a yes/no
+ *     decision taken in the precision of the GPU kernel: with zh = fl32(z), zl = fl32(z - zh),
+ *     r = (zh_j - zh_i) + (zl_j - zl_i) per component in FP32 and |r|^2 = fma(rx, rx,
+ *     fma(ry, ry, rz * rz)) in FP32, the pair is in iff |r|^2 <= fl32(cutoff^2).
  *   Medium order (Sec. 2: couples the FFT and far-field solvers; Sec. 6: uses FFTs for the
  *     change in vorticity): dz/dt = u from the Birkhoff-Rott sum, while Phi (hence dw/dt) takes
  *     the low-order velocity.
@@ -208,6 +213,42 @@ void zmo_br_velocity(size_t nt, const double *zt, size_t ns, const double *zs,
     }
 }
 
+/* Cutoff decision for target z_i and source z_j (component stride si, sj), FP32 as stated. */
+int zmo_within_cutoff(const double *zi, size_t si, const double *zj, size_t sj, double cutoff)
+{
+    float r[3];
+    for (int c = 0; c < 3; c++) {
+        float hi = (float)zi[c * si], hj = (float)zj[c * sj];
+        float li = (float)(zi[c * si] - (double)hi), lj = (float)(zj[c * sj] - (double)hj);
+        r[c] = (hj - hi) + (lj - li);
+    }
+    float r2 = fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]));
+    return r2 <= (float)(cutoff * cutoff);
+}
+
+void zmo_br_velocity_cutoff(size_t nt, const double *zt, size_t ns, const double *zs,
+                            const double *gamma, double weight, double delta, double cutoff,
+                            double *u)
+{
+    double pref = -weight / (4.0 * ZMO_PI);
+    double d2 = delta * delta;
+    for (size_t i = 0; i < nt; i++) {
+        nsum acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+        double xi = zt[i], yi = zt[nt + i], wi = zt[2 * nt + i];
+        for (size_t j = 0; j < ns; j++) {
+            if (!zmo_within_cutoff(zt + i, nt, zs + j, ns, cutoff)) continue;
+            double rx = xi - zs[j], ry = yi - zs[ns + j], rz = wi - zs[2 * ns + j];
+            double gx = gamma[j], gy = gamma[ns + j], gz = gamma[2 * ns + j];
+            double r2 = rx * rx + ry * ry + rz * rz + d2;
+            double k = 1.0 / (r2 * sqrt(r2));
+            nadd(&acc[0], (ry * gz - rz * gy) * k);
+            nadd(&acc[1], (rz * gx - rx * gz) * k);
+            nadd(&acc[2], (rx * gy - ry * gx) * k);
+        }
+        for (int c = 0; c < 3; c++) u[c * nt + i] = pref * (acc[c].s + acc[c].c);
+    }
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Low order: FFT Riesz-transform velocity (Sec. 2: FFT approximation of the BR integral).      */
 /* ------------------------------------------------------------------------------------------ */
@@ -334,7 +375,10 @@ int zmo_derivative(const zmo_mesh *m, const zmo_params *prm, const double *z, co
         double *gamma = malloc(3 * N * sizeof(double));
         zmo_sheet_strength(N, w, a1, a2, gamma);
         double weight = (m->L1 / m->n1) * (m->L2 / m->n2);
-        zmo_br_velocity(N, z, N, z, gamma, weight, prm->delta, u);
+        if (prm->cutoff > 0)
+            zmo_br_velocity_cutoff(N, z, N, z, gamma, weight, prm->delta, prm->cutoff, u);
+        else
+            zmo_br_velocity(N, z, N, z, gamma, weight, prm->delta, u);
         free(gamma);
     } else {
         memcpy(u, u_low, 3 * N * sizeof(double));

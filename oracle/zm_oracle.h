@@ -23,6 +23,7 @@ typedef struct {
 typedef struct {
     double atwood, g, mu, delta;
     int order;       /* ZMO_ORDER_LOW, ZMO_ORDER_MEDIUM or ZMO_ORDER_HIGH */
+    double cutoff;   /* > 0: Birkhoff-Rott sum over sources within this distance only */
 } zmo_params;
 
 /* All field arrays are component-major: f[c * n1 * n2 + i * n2 + j]. */
@@ -34,6 +35,10 @@ void zmo_sheet_strength(size_t N, const double *w, const double *a1, const doubl
                         double *gamma);
 void zmo_br_velocity(size_t nt, const double *zt, size_t ns, const double *zs,
                      const double *gamma, double weight, double delta, double *u);
+void zmo_br_velocity_cutoff(size_t nt, const double *zt, size_t ns, const double *zs,
+                            const double *gamma, double weight, double delta, double cutoff,
+                            double *u);
+int zmo_within_cutoff(const double *zi, size_t si, const double *zj, size_t sj, double cutoff);
 void zmo_fft2(int n1, int n2, double *re, double *im, int sign);
 void zmo_riesz_scalar(const zmo_mesh *m, const double *w, double *s);
 void zmo_phi(size_t N, const double *z, const double *w, const double *h, const double *u,

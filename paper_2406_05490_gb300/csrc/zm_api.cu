@@ -92,6 +92,7 @@ int batch_vorticity_rate(Batch *b, int yin);
 int batch_step(Batch *b, double dt, int nsteps);
 int batch_status(Batch *b);
 int batch_keep_phi(Batch *b, int on);
+int batch_set_cutoff(Batch *b, int index, double cutoff);
 int batch_autotune(Batch *b, const char *path, int *chosen, float *ms);
 
 static int stage_index(zm_ctx *c, const double *y) { return y == c->y0 ? 0 : (y == c->ya ? 1 : 2); }
@@ -496,6 +497,16 @@ int zm_check_finite(zm_ctx *c)
     if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream), "zm_check_finite");
     if (!rc && h) rc = set_error(ZM_ERR_NONFINITE, "zm_check_finite: state holds NaN or Inf");
     return rc;
+}
+
+int zm_set_cutoff(zm_ctx *c, double cutoff)
+{
+    if (!c || !(cutoff >= 0) || !std::isfinite(cutoff))
+        return set_error(ZM_ERR_INVALID, "zm_set_cutoff: bad arguments");
+    if (!c->batch)
+        return set_error(ZM_ERR_UNSUPPORTED, "zm_set_cutoff: the cutoff sum runs on FP32C contexts");
+    batch_bind(c->batch, c->stream, &c->prof);
+    return batch_set_cutoff(c->batch, 0, cutoff);
 }
 
 int zm_autotune(zm_ctx *c, const char *cache_path, int32_t *chosen)

@@ -532,6 +532,12 @@ int batch_step(Batch *b, double dt, int nsteps)
     return rc ? rc : b->step(nsteps, true);
 }
 int batch_status(Batch *b) { return b->status(); }
+int batch_set_cutoff(Batch *b, int index, double cutoff)
+{
+    for (int k = 0; k < (int)b->h.size(); ++k)
+        if (index < 0 || index == k) b->h[k].cutoff = cutoff;
+    return b->plan();
+}
 int batch_keep_phi(Batch *b, int on)
 {
     for (auto &I : b->h) I.keep_phi = on;
@@ -680,6 +686,13 @@ int zm_batch_autotune(zm_batch *bt, const char *cache_path, int32_t *chosen, flo
     int rc = bt->b.autotune(cache_path, &c, best_ms);
     if (chosen) *chosen = c;
     return rc;
+}
+
+int zm_batch_set_cutoff(zm_batch *bt, int32_t index, double cutoff)
+{
+    if (!bt || index < -1 || index >= (int32_t)bt->b.h.size() || !(cutoff >= 0) || !std::isfinite(cutoff))
+        return set_error(ZM_ERR_INVALID, "zm_batch_set_cutoff: bad arguments");
+    return batch_set_cutoff(&bt->b, index, cutoff);
 }
 
 int zm_batch_info(zm_batch *bt, int64_t *points, int64_t *pairs_per_eval, int64_t *work_items,

@@ -19,6 +19,13 @@
 //     more than a few units of FP32 rounding.  Two adjacent sources share one packed FP32x2
 //     instruction (fma/mul/add .f32x2), which halves issue slots for the same FP32 work.
 //
+// Cutoff (paper Sec. 3.2.2 CutoffBRSolver: only sources within a 3D distance of the target).
+// With a cutoff c, the tile spheres classify each (target tile, source tile): entirely beyond c
+// (skipped: no copy, no work), entirely within c (the paths above), or straddling c (the near
+// path with a per-pair test |r|^2 <= c^2 on the FP32 hi/lo difference).  Compact tiles of the
+// mesh act as the cell list.  A relative margin of 1e-4 on c keeps the sphere decisions on the
+// safe side of every pair decision.
+//
 // Accumulation.  Each (target, source tile) partial is an FP32 sum over 256 sources.  Partials
 // are added exactly in 64-bit fixed point, value * 2^S with S per interface chosen from the
 // bound |u| <= N max|gamma'| (2 / (3 sqrt 3)) / delta^2 so that no sum can overflow.  Integer
@@ -118,46 +125,55 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
     int p_inst = 0, p_tile = 0, p_next = 0, p_left = 0;
     bool p_done = false;
     auto produce = [&](int buf) {
-        while (p_left == 0 && !p_done) {
-            const long long it = (long long)atomicAdd(counter, 1ull);
-            if (it >= nitems) {
-                p_done = true;
-                break;
+        while (true) {
+            while (p_left == 0 && !p_done) {
+                const long long it = (long long)atomicAdd(counter, 1ull);
+                if (it >= nitems) {
+                    p_done = true;
+                    break;
+                }
+                int lo = 0, hi = ninst - 1;  // last interface with item0 <= it
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (insts[mid].item0 <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                const Inst &I = insts[lo];
+                const long long local = it - I.item0;
+                p_inst = lo;
+                p_tile = (int)(local / I.nchunks);
+                const int ch = (int)(local - (long long)p_tile * I.nchunks);
+                p_next = ch * I.chunk;
+                p_left = min(I.chunk, I.tiling.ntiles - p_next);
             }
-            int lo = 0, hi = ninst - 1;  // last interface with item0 <= it
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (insts[mid].item0 <= it) lo = mid;
-                else hi = mid - 1;
+            if (p_done) {
+                unit[buf].inst = -1;
+                return;
             }
-            const Inst &I = insts[lo];
-            const long long local = it - I.item0;
-            p_inst = lo;
-            p_tile = (int)(local / I.nchunks);
-            const int ch = (int)(local - (long long)p_tile * I.nchunks);
-            p_next = ch * I.chunk;
-            p_left = min(I.chunk, I.tiling.ntiles - p_next);
-        }
-        if (p_done) {
-            unit[buf].inst = -1;
+            const Inst &I = insts[p_inst];
+            const int S = p_next++;
+            --p_left;
+            const float4 a = I.tinfo[p_tile], b = I.tinfo[S];
+            const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+            const float D = sqrtf(dx * dx + dy * dy + dz * dz);
+            int path = (D >= kFarFactor * (a.w + b.w)) ? 1 : 0;  // 1 far, 0 near
+            if (I.cutoff > 0.0) {
+                const float c = (float)I.cutoff;
+                if (D - a.w - b.w > c * 1.0001f) continue;          // every pair beyond c
+                if (D + a.w + b.w >= c * 0.9999f) path = 2;         // straddles c: masked near
+            }
+            unit[buf].inst = p_inst;
+            unit[buf].tile = p_tile;
+            unit[buf].src = S;
+            unit[buf].far = path;
+            if (path == 1)
+                dev::tma_load_1d(stage[buf], I.far_rec + (size_t)S * kRec32F * kTs,
+                                 kRec32F * kTs * sizeof(float), &bar[buf]);
+            else
+                dev::tma_load_1d(stage[buf], I.near_rec + (size_t)S * kRec32 * kTs,
+                                 kRec32 * kTs * sizeof(float), &bar[buf]);
             return;
         }
-        const Inst &I = insts[p_inst];
-        const int S = p_next++;
-        --p_left;
-        const float4 a = I.tinfo[p_tile], b = I.tinfo[S];
-        const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-        const bool far = sqrtf(dx * dx + dy * dy + dz * dz) >= kFarFactor * (a.w + b.w);
-        unit[buf].inst = p_inst;
-        unit[buf].tile = p_tile;
-        unit[buf].src = S;
-        unit[buf].far = far ? 1 : 0;
-        if (far)
-            dev::tma_load_1d(stage[buf], I.far_rec + (size_t)S * kRec32F * kTs,
-                             kRec32F * kTs * sizeof(float), &bar[buf]);
-        else
-            dev::tma_load_1d(stage[buf], I.near_rec + (size_t)S * kRec32 * kTs,
-                             kRec32 * kTs * sizeof(float), &bar[buf]);
     };
 
     if (tid == 0) {
@@ -176,7 +192,7 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
 
     // ---- consumer state (all threads) ----
     int c_inst = -1, c_tile = -1;
-    float c_d2 = 0.0f, c_mult = 1.0f;
+    float c_d2 = 0.0f, c_mult = 1.0f, c_c2 = 0.0f;
     const float *c_near = nullptr;
 
     auto flush = [&]() {
@@ -213,6 +229,7 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
                 const int sc = fix_scale(I);
                 c_mult = __int_as_float((127 + sc) << 23);  // 2^scale, exact
                 c_d2 = (float)(I.delta * I.delta);
+                c_c2 = (float)(I.cutoff * I.cutoff);
                 c_near = I.near_rec;
                 if (tid == 0) *I.scale = sc;
             }
@@ -221,7 +238,7 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
         }
         if (ok) {
             const float *s = stage[b];
-            if (un.far) {
+            if (un.far == 1) {
                 // ---- far path ------------------------------------------------------------
                 const float4 cs = insts[c_inst].tinfo[un.src];
                 u64 m2x[kR], m2y[kR], m2z[kR], bb[kR];
@@ -271,7 +288,8 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
                     acc[2][r][tid] += __float2ll_rn(vz * c_mult);
                 }
             } else {
-                // ---- near path -----------------------------------------------------------
+                // ---- near path (masked at the cutoff when the tile straddles it) ---------
+                const float c2 = (un.far == 2) ? c_c2 : __int_as_float(0x7f800000);
                 float hx[kR], hy[kR], hz[kR], lx[kR], ly[kR], lz[kR], px[kR], py[kR], pz[kR];
 #pragma unroll
                 for (int r = 0; r < kR; ++r) {
@@ -296,7 +314,8 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
                         const float rz = (shz - hz[r]) + (slz - lz[r]);
                         const float q = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, c_d2)));
                         const float iq = dev::rsqrt_approx(q);
-                        const float kk = iq * iq * iq;
+                        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                        const float kk = (r2 <= c2) ? iq * iq * iq : 0.0f;
                         px[r] = fmaf(kk, fmaf(ry, gz, -rz * gy), px[r]);
                         py[r] = fmaf(kk, fmaf(rz, gx, -rx * gz), py[r]);
                         pz[r] = fmaf(kk, fmaf(rx, gy, -ry * gx), pz[r]);

@@ -75,6 +75,7 @@ struct Inst {
     double atwood, g, mu, delta;
     double dt;                  // RK3 step of this interface
     int keep_phi;               // medium order: Phi comes from the FFT velocity, not from u
+    double cutoff;              // > 0: sum only over sources within this distance
     int block0;                 // first 256-thread block of this interface in the point kernels
     int chunk, nchunks;         // source tiles per Birkhoff-Rott work item; items per target tile
     long long item0;            // first Birkhoff-Rott work item of this interface

@@ -109,6 +109,8 @@ def load():
             "zm_batch_autotune": (I, [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_float)]),
             "zm_autotune": (I, [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]),
+            "zm_set_cutoff": (I, [VP, D]),
+            "zm_batch_set_cutoff": (I, [VP, ctypes.c_int32, D]),
             "zm_batch_info": (I, [VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
             "zm_batch_set_profiling": (I, [VP, I]),
@@ -296,6 +298,14 @@ def zm_batch_autotune(h, cache_path=None):
     p = cache_path.encode() if cache_path else None
     _check(load().zm_batch_autotune(h, p, ctypes.byref(c), ctypes.byref(ms)))
     return c.value, ms.value
+
+
+def zm_set_cutoff(h, cutoff):
+    _check(load().zm_set_cutoff(h, float(cutoff)))
+
+
+def zm_batch_set_cutoff(h, index, cutoff):
+    _check(load().zm_batch_set_cutoff(h, int(index), float(cutoff)))
 
 
 def zm_autotune(h, cache_path=None):

@@ -310,6 +310,28 @@ def test_brute_force_50_digits():
         np.testing.assert_allclose(u[:, i], ref, rtol=0, atol=1e-14 * np.abs(ref).max())
 
 
+def test_cutoff_sum_decomposes_the_exact_sum():
+    """The cutoff sum plus the exact sum over the excluded sources (chosen here by explicit
+    distances) is the exact sum; a cutoff past the cloud's diameter is the exact sum itself and
+    one below the smallest distance leaves only the (zero) self term."""
+    rng = np.random.default_rng(23)
+    N = 300
+    z = rng.uniform(0, 1, size=(3, N)) * np.array([[1.0], [1.0], [0.2]])
+    gam = rng.normal(size=(3, N))
+    wt, de, c = 1e-3, 0.01, 0.3
+    ucut = oracle.br_velocity_cutoff(z, z, gam, wt, de, c)
+    uex = oracle.br_velocity(z, z, gam, wt, de)
+    dist = np.linalg.norm(z[:, :, None] - z[:, None, :], axis=0)
+    for i in range(0, N, 7):
+        far = np.where(dist[i] > c * (1 + 1e-6))[0]
+        border = np.where(np.abs(dist[i] - c) <= c * 1e-6)[0]
+        assert len(border) == 0  # no pair sits on the FP32 decision boundary in this cloud
+        ufar = oracle.br_velocity(z[:, [i]], z[:, far], gam[:, far], wt, de)[:, 0]
+        np.testing.assert_allclose(ucut[:, i] + ufar, uex[:, i], rtol=0, atol=1e-13 * np.abs(uex[:, i]).max())
+    assert np.array_equal(oracle.br_velocity_cutoff(z, z, gam, wt, de, 10.0), uex)
+    assert np.all(oracle.br_velocity_cutoff(z, z, gam, wt, de, 1e-6) == 0.0)
+
+
 # ------------------------------------------------------------------------------------------
 # Riesz transform / FFT
 # ------------------------------------------------------------------------------------------

@@ -505,6 +505,19 @@ def run_gb300(args):
             # write u (24) + Phi (8)
             "riesz_alg_gbs": 80 * nl * nl / (fft_ms * 1e-3) / 1e9,
             "kernel_ms_per_step": {k: v / kl for k, v in profl["ms"].items()}}
+        # paper-scale low order (NEXT row 3): 4096^2 = 16.8 M points, the largest power-of-two
+        # side below the paper's 4864^2 base mesh
+        nb = 4096
+        zb, wb = inputs.multi_mode(nb, n_modes=8, seed=7, amp=0.02)
+        mb = zm.ZModel(nb, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW)
+        mb.set_state(zb, wb)
+        del zb, wb
+        kb = 3
+        msb, profb = timed_steps(mb, zm, torch, kb, 1, flush)
+        mb.close()
+        extras["low_order_4096"] = {"steps_per_s": kb / (msb * 1e-3), "ms_per_step": msb / kb,
+                                    "points": nb * nb,
+                                    "kernel_ms_per_step": {k: v / kb for k, v in profb["ms"].items()}}
         # 32^2 single-mode FP64 (launch bound)
         zs, wsn = inputs.single_mode(32)
         ms_ = zm.ZModel(32, periodic=False, atwood=0.5, g=1.0, delta=0.1 / 32)

@@ -205,6 +205,22 @@ def test_low_order_1024_full(zm):
     assert eu <= TOL64 and ew <= TOL64
 
 
+def test_low_order_2048_full(zm):
+    """Low order at 2048^2 (4.2 M points; every field larger than L2 together): all of u and
+    dw/dt against the oracle."""
+    n = 2048
+    z, _ = inputs.multi_mode(n, n_modes=8, seed=5, amp=0.02)
+    _, w = inputs.random_state(n, seed=14)
+    m = oracle.Mesh(n, periodic=True)
+    u_ref, wd_ref = oracle.derivative(m, z, w, 0.7, 1.0, 0.0, 0.0, order=oracle.ORDER_LOW)
+    model = zm.ZModel(n, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW)
+    u, wd = model.velocity(z, w)
+    model.close()
+    eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+    print(f"low order 2048^2: rel L2 u={eu:.3e} wdot={ew:.3e}")
+    assert eu <= TOL64 and ew <= TOL64
+
+
 def test_deterministic_and_device_pointers(zm):
     import torch
     n = 48

@@ -34,6 +34,19 @@ sys.path.insert(0, ROOT)
 METRIC = "BR G-pair-interactions/s & Z-Model steps/s vs plain FP64; serve p50/p99 ms"
 UNIT = "Gpair/s"
 N_SIDE = 256
+
+
+def _measured_hbm_gbs(default=6795.5):
+    """Copy bandwidth (read + write bytes) measured on this GPU model, from the peaks file at the
+    repository root when present."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return default
+
+
+HBM_GBS = _measured_hbm_gbs()
 FLOPS_PER_PAIR = 26  # direct-formula FP32 flops per pair interaction (FMA = 2; rsqrt on MUFU)
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 CONFIG = {"workload": "multimode-256x256-highorder-fp32c", "n_side": N_SIDE, "points": N_SIDE**2,
@@ -229,6 +242,44 @@ def timed_steps(model, zm, torch, steps, warmup, flush, profile=True):
     prof = zm.zm_get_profile(model.h)
     zm.zm_set_profiling(model.h, 0)
     return ms, prof
+
+
+# Algorithmic HBM bytes per mesh point of each low-order kernel class and launch (8 bytes per
+# value in FP64 and in double-word storage alike):
+#   geometry   reads z, w (40), writes the normal and q (32);
+#   fft        three passes: w -> spectrum (16 + 16), spectrum -> filtered (16 + 16), filtered,
+#              normal, q -> u, Phi (48 + 32); the method's floor, one pass reading w, N, q and
+#              writing u, Phi, is 80 B;
+#   vorticity  reads Phi, y, u, y0 (112), writes the next stage (40).
+LOW_BYTES = {"geometry": 72, "fft": 144, "vorticity": 152}
+LOW_LAUNCHES_PER_EVAL = {"geometry": 1, "fft": 3, "vorticity": 1}
+
+
+def bench_low_order(zm, torch, inputs, flush, nl, steps, warmup, df64):
+    """Low-order steps on an nl^2 periodic 8-mode interface (amplitude 0.02, A = 0.7): device
+    time per step, and per kernel class its time per evaluation and algorithmic HBM GB/s as a
+    fraction of the measured copy bandwidth."""
+    zl, wl = inputs.multi_mode(nl, n_modes=8, seed=7, amp=0.02)
+    ml = zm.ZModel(nl, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW, df64=df64)
+    ml.set_state(zl, wl)
+    del zl, wl
+    msl, profl = timed_steps(ml, zm, torch, steps, warmup, flush)
+    ml.close()
+    pts = nl * nl
+    kern = {}
+    for k, b in LOW_BYTES.items():
+        evals = max(profl["launches"][k] // LOW_LAUNCHES_PER_EVAL[k], 1)
+        t = profl["ms"][k] / evals
+        gbs = b * pts / (t * 1e-3) / 1e9 if t > 0 else 0.0
+        kern[k] = {"ms_per_eval": t, "alg_bytes_per_point": b, "alg_gbs": gbs, "hbm_frac": gbs / HBM_GBS}
+    step_bytes = 3 * sum(LOW_BYTES.values()) * pts
+    return {"precision": "double-word (FP32 pairs)" if df64 else "fp64", "points": pts,
+            "steps": steps, "steps_per_s": steps / (msl * 1e-3), "ms_per_step": msl / steps,
+            "step_alg_gbs": step_bytes / (msl / steps * 1e-3) / 1e9,
+            "step_hbm_frac": step_bytes / (msl / steps * 1e-3) / 1e9 / HBM_GBS,
+            "riesz_floor_gbs": 80 * pts / (kern["fft"]["ms_per_eval"] * 1e-3) / 1e9
+            if kern["fft"]["ms_per_eval"] > 0 else 0.0,
+            "kernels": kern, "hbm_peak_gbs": HBM_GBS, "hbm_peak_basis": "measured copy bandwidth"}
 
 
 def bench_batched(zm, torch, inputs, flush, steps=10, warmup=2, count=64):
@@ -488,36 +539,12 @@ def run_gb300(args):
                                 "steps_per_s": k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64,
                                 "steps": k64}
         extras["fp32c_speedup_vs_fp64"] = value / ws / extras["fp64_plain"]["gpairs_per_s"]
-        # low-order 1024^2 FFT Riesz step
-        nl = 1024
-        zl, wl = inputs.multi_mode(nl, n_modes=8, seed=7, amp=0.02)
-        ml = zm.ZModel(nl, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW)
-        ml.set_state(zl, wl)
-        kl = 10
-        msl, profl = timed_steps(ml, zm, torch, kl, 3, flush)
-        ml.close()
-        nfft = max(profl["launches"]["fft"] // 3, 1)
-        fft_ms = profl["ms"]["fft"] / nfft
-        extras["low_order_1024"] = {
-            "steps_per_s": kl / (msl * 1e-3), "ms_per_step": msl / kl,
-            "riesz_ms_per_eval": fft_ms,
-            # algorithmic bytes of one Riesz evaluation: read w (16 B/pt) + normal (24) + q (8),
-            # write u (24) + Phi (8)
-            "riesz_alg_gbs": 80 * nl * nl / (fft_ms * 1e-3) / 1e9,
-            "kernel_ms_per_step": {k: v / kl for k, v in profl["ms"].items()}}
-        # paper-scale low order (NEXT row 3): 4096^2 = 16.8 M points, the largest power-of-two
-        # side below the paper's 4864^2 base mesh
-        nb = 4096
-        zb, wb = inputs.multi_mode(nb, n_modes=8, seed=7, amp=0.02)
-        mb = zm.ZModel(nb, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW)
-        mb.set_state(zb, wb)
-        del zb, wb
-        kb = 3
-        msb, profb = timed_steps(mb, zm, torch, kb, 1, flush)
-        mb.close()
-        extras["low_order_4096"] = {"steps_per_s": kb / (msb * 1e-3), "ms_per_step": msb / kb,
-                                    "points": nb * nb,
-                                    "kernel_ms_per_step": {k: v / kb for k, v in profb["ms"].items()}}
+        # low order (FFT Riesz velocity): 1024^2 (the low-vs-high configuration), FP64 and
+        # double-word; 4096^2, the largest power-of-two side below the paper's 4864^2 mesh
+        extras["low_order_1024"] = bench_low_order(zm, torch, inputs, flush, 1024, 10, 3, False)
+        extras["low_order_1024_df64"] = bench_low_order(zm, torch, inputs, flush, 1024, 10, 3, True)
+        extras["low_order_4096"] = bench_low_order(zm, torch, inputs, flush, 4096, 3, 1, False)
+        extras["low_order_4096_df64"] = bench_low_order(zm, torch, inputs, flush, 4096, 5, 2, True)
         # 32^2 single-mode FP64 (launch bound)
         zs, wsn = inputs.single_mode(32)
         ms_ = zm.ZModel(32, periodic=False, atwood=0.5, g=1.0, delta=0.1 / 32)

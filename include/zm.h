@@ -66,6 +66,13 @@ extern "C" {
 #define ZM_PREC_FP32C 0x100 /* BR pair terms in FP32 (hi/lo positions near, tile-local
                                coordinates far), per-tile FP32 partials, exact 64-bit fixed-point
                                accumulation across tiles (finer than FP64); all else FP64 */
+#define ZM_PREC_DF64 0x200  /* low order only: every stencil, FFT and RK3 operation in
+                               double-word arithmetic (pairs of FP32 numbers, ~48-bit significand,
+                               FP32 exponent range) instead of FP64 instructions; the resident
+                               state is held as FP32 pairs with z1, z2 relative to the mesh
+                               coordinates and converted at zm_set_state / zm_get_state /
+                               zm_velocity.  Not in the paper: an implementation choice for GPUs
+                               whose FP64 rate is far below their FP32 rate */
 
 typedef struct {
     int32_t n1, n2;   /* nodes along alpha1 (slow index i) and alpha2 (fast index j), >= 5 */
@@ -80,7 +87,8 @@ typedef struct zm_ctx zm_ctx;
  * and workspace (owned by the context until zm_destroy).  delta > 0 is the Birkhoff-Rott core
  * size (high order); mu >= 0 the artificial viscosity; `order` is ZM_ORDER_* | ZM_PREC_*.
  * Returns ZM_ERR_UNSUPPORTED for low or medium order on a free-edge mesh or a non power-of-two
- * side. */
+ * side, and for ZM_PREC_DF64 with medium or high order; ZM_ERR_INVALID for ZM_PREC_FP32C
+ * combined with ZM_PREC_DF64. */
 int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double delta, int order,
               zm_ctx **out);
 

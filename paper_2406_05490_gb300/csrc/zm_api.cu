@@ -113,6 +113,7 @@ int derivative(zm_ctx *c, const double *y)
         }
         return batch_derivative(c->batch, stage_index(c, y));
     }
+    if (c->df64) return df_derivative(c, y);
     int rc = launch_geometry(c, y);
     if (rc) return rc;
     if (c->order == ZM_ORDER_LOW) return launch_riesz(c, y);
@@ -227,8 +228,11 @@ int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double de
     *out = nullptr;
     const int ord = order & 0xff;
     const int fp32c = (order & ZM_PREC_FP32C) ? 1 : 0;
-    if ((order & ~(0xff | ZM_PREC_FP32C)) != 0 || ord > ZM_ORDER_HIGH)
+    const int df64 = (order & ZM_PREC_DF64) ? 1 : 0;
+    if ((order & ~(0xff | ZM_PREC_FP32C | ZM_PREC_DF64)) != 0 || ord > ZM_ORDER_HIGH || (fp32c && df64))
         return set_error(ZM_ERR_INVALID, "zm_create: unknown order/precision flags");
+    if (df64 && ord != ZM_ORDER_LOW)
+        return set_error(ZM_ERR_UNSUPPORTED, "zm_create: double-word precision is built for low order only");
     if (mesh->n1 < 5 || mesh->n2 < 5 || (int64_t)mesh->n1 * mesh->n2 > (1 << 26))
         return set_error(ZM_ERR_INVALID, "zm_create: mesh sides must be >= 5 and n1*n2 <= 2^26");
     if (!(mesh->L1 > 0) || !(mesh->L2 > 0) || !std::isfinite(mesh->L1) || !std::isfinite(mesh->L2))
@@ -257,6 +261,7 @@ int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double de
     c->delta = delta;
     c->order = ord;
     c->fp32c = fp32c;
+    c->df64 = df64;
     c->stream = nullptr;
     cudaGetDevice(&c->device);
     Geom &G = c->geom;
@@ -325,7 +330,7 @@ int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double de
         return set_error(ZM_ERR_NOMEM, "zm_create: device allocation failed");
     }
     if (fft) {
-        int rc = fft_setup(c);
+        int rc = df64 ? df_setup(c) : fft_setup(c);
         if (rc) {
             zm_destroy(c);
             return rc;
@@ -351,8 +356,10 @@ int zm_set_state(zm_ctx *c, const double *z, const double *w)
 {
     if (!c || !z || !w) return set_error(ZM_ERR_INVALID, "zm_set_state: null argument");
     const size_t N = c->geom.N;
-    int rc = copy_in(c, c->y0, z, 3 * N);
-    if (!rc) rc = copy_in(c, c->y0 + 3 * N, w, 2 * N);
+    double *dst = c->df64 ? c->yb : c->y0;  // double word: stage FP64 in yb, convert into y0
+    int rc = copy_in(c, dst, z, 3 * N);
+    if (!rc) rc = copy_in(c, dst + 3 * N, w, 2 * N);
+    if (!rc && c->df64) rc = df_convert(c, c->yb, c->y0, 5 * N, 1, 1);
     if (!rc && (!is_device_ptr(z) || !is_device_ptr(w)))
         rc = cuda_check(cudaStreamSynchronize(c->stream), "zm_set_state");
     return rc;
@@ -364,8 +371,13 @@ int zm_get_state(zm_ctx *c, double *z, double *w)
     const size_t N = c->geom.N;
     bool host = false;
     int rc = ZM_OK;
-    if (z) rc = copy_out(c, z, c->y0, 3 * N, &host);
-    if (!rc && w) rc = copy_out(c, w, c->y0 + 3 * N, 2 * N, &host);
+    const double *src = c->y0;
+    if (c->df64) {  // FP64 copy of the state in yb (a stage buffer, free between calls)
+        rc = df_convert(c, c->y0, c->yb, 5 * N, 1, 0);
+        src = c->yb;
+    }
+    if (!rc && z) rc = copy_out(c, z, src, 3 * N, &host);
+    if (!rc && w) rc = copy_out(c, w, src + 3 * N, 2 * N, &host);
     if (!rc && host) rc = read_status(c);
     return rc;
 }
@@ -379,12 +391,24 @@ int zm_velocity(zm_ctx *c, const double *z, const double *w, double *u, double *
     const double *y = c->y0;
     int rc = ZM_OK;
     if (z) {
-        rc = copy_in(c, c->ya, z, 3 * N);
-        if (!rc) rc = copy_in(c, c->ya + 3 * N, w, 2 * N);
+        double *dst = c->df64 ? c->yb : c->ya;
+        rc = copy_in(c, dst, z, 3 * N);
+        if (!rc) rc = copy_in(c, dst + 3 * N, w, 2 * N);
+        if (!rc && c->df64) rc = df_convert(c, c->yb, c->ya, 5 * N, 1, 1);
         y = c->ya;
     }
     if (!rc) rc = derivative(c, y);
     bool host = false;
+    if (!rc && c->df64) {
+        // dw/dt as double words into yb[3N, 5N), then both fields to FP64 in yb
+        if (wdot) rc = df_vorticity(c, y, c->yb + 3 * N, nullptr, nullptr, 0, 0, 0, 0);
+        if (!rc && wdot) rc = df_convert(c, c->yb + 3 * N, c->yb + 3 * N, 2 * N, 0, 0);
+        if (!rc) rc = df_convert(c, c->u, c->yb, 3 * N, 0, 0);
+        if (!rc && wdot) rc = copy_out(c, wdot, c->yb + 3 * N, 2 * N, &host);
+        if (!rc) rc = copy_out(c, u, c->yb, 3 * N, &host);
+        if (!rc && host) rc = read_status(c);
+        return rc;
+    }
     if (!rc && wdot && c->batch) {
         rc = batch_vorticity_rate(c->batch, stage_index(c, y));  // dw/dt into yb[0, 2N)
         if (!rc) rc = copy_out(c, wdot, c->yb, 2 * N, &host);
@@ -410,7 +434,8 @@ static int rk3_step_launches(zm_ctx *c, double dt)
     double *yout[3] = {c->ya, c->yb, c->y0};
     for (int st = 0; st < 3; ++st) {
         int rc = derivative(c, yin[st]);
-        if (!rc) rc = launch_vorticity(c, yin[st], nullptr, c->y0, yout[st], dt, ca[st], cb[st], 1);
+        if (!rc && c->df64) rc = df_vorticity(c, yin[st], nullptr, c->y0, yout[st], dt, ca[st], cb[st], 1);
+        else if (!rc) rc = launch_vorticity(c, yin[st], nullptr, c->y0, yout[st], dt, ca[st], cb[st], 1);
         if (rc) return rc;
     }
     return ZM_OK;
@@ -490,7 +515,8 @@ int zm_step(zm_ctx *c, double dt, int nsteps)
 int zm_check_finite(zm_ctx *c)
 {
     if (!c) return set_error(ZM_ERR_INVALID, "zm_check_finite: null context");
-    int rc = check_finite(c, c->y0, 5 * (size_t)c->geom.N, c->flag);
+    int rc = c->df64 ? df_check_finite(c, c->y0, 5 * (size_t)c->geom.N, c->flag)
+                     : check_finite(c, c->y0, 5 * (size_t)c->geom.N, c->flag);
     int h = 0;
     if (!rc) rc = cuda_check(cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
                              "finite flag read");

@@ -1,0 +1,136 @@
+// zm_df64.cuh -- double-word arithmetic on pairs of FP32 numbers ("double-float").
+//
+// A value is x = hi + lo with |lo| <= ulp(hi) / 2, about 48 significant bits (unit roundoff
+// u^2 = 2^-48 ~ 3.6e-15) in the FP32 exponent range.  GB300 runs FP32 FMA at ~75x its FP64
+// rate, so a double-word operation of 6-20 FP32 instructions is several times cheaper than
+// one FP64 instruction; the low-order path (stencils, FFT Riesz velocity, RK3 combine) uses
+// this arithmetic to stay within FP64-class tolerances without the FP64 pipe.
+//
+// Building blocks (published error-free transformations, restated here):
+//   two_sum       Knuth's TwoSum: s + e == a + b exactly, 6 flops, no precondition;
+//   fast_two_sum  Dekker's Fast2Sum: exact when |a| >= |b| (or a == 0), 3 flops;
+//   two_prod      p + e == a * b exactly with one FMA (e = fma(a, b, -p)), 2 flops;
+// and the double-word algorithms analysed by Joldes, Muller and Popescu (ACM TOMS 44, 2017):
+//   add    "sloppy" sum: error <= c u^2 (|x| + |y|), 11 flops -- normwise accurate, which is
+//          what FFT butterflies and sums of like-signed terms need;
+//   add_acc accurate sum: relative error <= 3 u^2 even under cancellation, 20 flops;
+//   mul    product without the lo*lo term: relative error <= 5 u^2, 8 flops;
+//   mul_f  product by an FP32 number: relative error <= 2 u^2, 6 flops.
+// Every operation uses the _rn intrinsics, which the compiler never contracts into FMAs or
+// reassociates, so the error-free transformations stay exact.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace zm {
+namespace dw {
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df mk(float hi, float lo) { return df{hi, lo}; }
+__device__ __forceinline__ df from_f(float a) { return df{a, 0.0f}; }
+__device__ __forceinline__ df from_f2(float2 v) { return df{v.x, v.y}; }
+__device__ __forceinline__ float2 to_f2(df a) { return make_float2(a.hi, a.lo); }
+
+__device__ __forceinline__ df two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df{s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return df{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return df{p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ df neg(df a) { return df{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df add(df x, df y)
+{
+    const df s = two_sum(x.hi, y.hi);
+    const float w = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return fast_two_sum(s.hi, w);
+}
+
+__device__ __forceinline__ df sub(df x, df y) { return add(x, neg(y)); }
+
+__device__ __forceinline__ df add_acc(df x, df y)
+{
+    const df s = two_sum(x.hi, y.hi);
+    const df t = two_sum(x.lo, y.lo);
+    const df v = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
+}
+
+__device__ __forceinline__ df sub_acc(df x, df y) { return add_acc(x, neg(y)); }
+
+__device__ __forceinline__ df mul(df x, df y)
+{
+    const df p = two_prod(x.hi, y.hi);
+    const float t = __fmaf_rn(x.lo, y.hi, __fmul_rn(x.hi, y.lo));
+    return fast_two_sum(p.hi, __fadd_rn(p.lo, t));
+}
+
+__device__ __forceinline__ df mul_f(df x, float b)
+{
+    const df p = two_prod(x.hi, b);
+    return fast_two_sum(p.hi, __fmaf_rn(x.lo, b, p.lo));
+}
+
+__device__ __forceinline__ df sqr(df x)
+{
+    const df p = two_prod(x.hi, x.hi);
+    return fast_two_sum(p.hi, __fmaf_rn(__fadd_rn(x.hi, x.hi), x.lo, p.lo));
+}
+
+// Multiplication by a power of two: exact (barring under/overflow).
+__device__ __forceinline__ df scale2(df x, float pow2) { return df{__fmul_rn(x.hi, pow2), __fmul_rn(x.lo, pow2)}; }
+
+// 1 / sqrt(x) for x > 0.  y0 = FP32 estimate (relative error e0 ~ 2^-22).  The residual
+// r = 1 - x y0^2 is formed in double-word arithmetic (y0^2 exact by two_prod, 1 - t.hi exact by
+// Sterbenz's lemma) and the binomial series y = y0 (1 + r/2 + 3 r^2/8) is applied with the
+// leading product y0 r exact, so the result carries the truncation O(e0^3) ~ 2^-66 and a few
+// u^2 of rounding (an FP32-rounding emulation measured <= 1.6 u^2 over [0.01, 100]).
+__device__ __forceinline__ df rsqrt(df x)
+{
+    const float y0 = rsqrtf(x.hi);
+    const df t = mul(x, two_prod(y0, y0));
+    const df r = two_sum(__fsub_rn(1.0f, t.hi), -t.lo);
+    const df c = two_prod(y0, r.hi);  // y0 r.hi, exact
+    const float rest = __fmaf_rn(y0, r.lo, __fmul_rn(__fmul_rn(c.hi, 0.75f), r.hi));
+    const df s = fast_two_sum(y0, __fmul_rn(0.5f, c.hi));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fmul_rn(0.5f, __fadd_rn(c.lo, rest))));
+}
+
+// Complex double-word number, stored as float4 {re.hi, re.lo, im.hi, im.lo}.
+struct cdf {
+    df re, im;
+};
+
+__device__ __forceinline__ cdf ld_c(float4 v) { return cdf{df{v.x, v.y}, df{v.z, v.w}}; }
+__device__ __forceinline__ float4 st_c(cdf a) { return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+__device__ __forceinline__ cdf cadd(cdf a, cdf b) { return cdf{add(a.re, b.re), add(a.im, b.im)}; }
+__device__ __forceinline__ cdf csub(cdf a, cdf b) { return cdf{sub(a.re, b.re), sub(a.im, b.im)}; }
+__device__ __forceinline__ cdf cmul(cdf a, cdf b)
+{
+    return cdf{sub(mul(a.re, b.re), mul(a.im, b.im)), add(mul(a.re, b.im), mul(a.im, b.re))};
+}
+// a * (+i) when s > 0, a * (-i) when s < 0: exact (a swap and a sign).
+__device__ __forceinline__ cdf cmul_pm_i(cdf a, int s)
+{
+    return s > 0 ? cdf{neg(a.im), a.re} : cdf{a.im, neg(a.re)};
+}
+
+}  // namespace dw
+}  // namespace zm

@@ -98,6 +98,7 @@ struct zm_ctx {
     double atwood, g, mu, delta;
     int order;  // ZM_ORDER_*
     int fp32c;  // reduced-precision Birkhoff-Rott pair terms
+    int df64;   // low order in double-word arithmetic: every field below is float2 pairs
     int device;
     cudaStream_t stream;
 
@@ -174,6 +175,18 @@ void init_far_records(float *far_rec, int ntiles, float d2, cudaStream_t s);
 // ---- low order (zm_fft.cu) ---------------------------------------------------------------------
 int fft_setup(zm_ctx *c);
 int launch_riesz(zm_ctx *c, const double *y);
+
+// ---- low order in double-word (FP32-pair) arithmetic (zm_lowdf.cu) -----------------------------
+// Buffers keep their FP64 sizes; a double-word context stores float2 {hi, lo} per value, with z1
+// and z2 as displacements from the mesh coordinates.
+int df_setup(zm_ctx *c);
+int df_derivative(zm_ctx *c, const double *y);
+int df_vorticity(zm_ctx *c, const double *y, double *wdot_out, const double *y0, double *yout,
+                 double dt, double ca, double cb, int mode);
+// count values src -> dst, FP64 -> double word (to_df) or back; `state`: src/dst hold the 5N
+// state and z1, z2 are taken relative to the mesh coordinates.  src may equal dst.
+int df_convert(zm_ctx *c, const double *src, double *dst, size_t count, int state, int to_df);
+int df_check_finite(zm_ctx *c, const double *y, size_t nvalues, int *dev_flag);
 
 // ---- one full derivative evaluation (zm_api.cu) --------------------------------------------------
 int derivative(zm_ctx *c, const double *y);

@@ -2,6 +2,7 @@
 configuration through the C ABI, nothing else.
 
     python -m paper_2406_05490_gb300.profile_cases low 2048 3      # low order, 2048^2, 3 steps
+    python -m paper_2406_05490_gb300.profile_cases lowdf 2048 3    # the same in double words
     python -m paper_2406_05490_gb300.profile_cases high32 256 2     # FP32C high order
     python -m paper_2406_05490_gb300.profile_cases high64 128 2     # FP64 high order
     python -m paper_2406_05490_gb300.profile_cases batch 64 2       # 64 ragged interfaces
@@ -30,10 +31,11 @@ def main(argv):
         zm.zm_batch_sync(h)
         zm.zm_batch_destroy(h)
         return 0
-    order = zm.ZM_ORDER_LOW if kind == "low" else zm.ZM_ORDER_HIGH
+    order = zm.ZM_ORDER_LOW if kind in ("low", "lowdf") else zm.ZM_ORDER_HIGH
     z, _ = inputs.multi_mode(size, n_modes=8, seed=7, amp=0.02)
     _, w = inputs.random_state(size, seed=3)
-    model = zm.ZModel(size, periodic=True, atwood=0.7, g=1.0, order=order, fp32c=(kind == "high32"))
+    model = zm.ZModel(size, periodic=True, atwood=0.7, g=1.0, order=order, fp32c=(kind == "high32"),
+                      df64=(kind == "lowdf"))
     model.set_state(z, w)
     model.step(1e-3, steps)
     model.sync()

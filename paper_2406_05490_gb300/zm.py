@@ -29,6 +29,7 @@ ZM_ORDER_MEDIUM = 1
 ZM_ORDER_HIGH = 2
 ZM_PREC_FP64 = 0x000
 ZM_PREC_FP32C = 0x100
+ZM_PREC_DF64 = 0x200
 
 ZM_K_GEOMETRY, ZM_K_BR, ZM_K_REDUCE, ZM_K_VORT, ZM_K_FFT, ZM_K_COUNT = range(6)
 KERNEL_NAMES = ["geometry", "br", "reduce", "vorticity", "fft"]
@@ -401,11 +402,11 @@ class ZModel:
     """One interface on the current GPU; owns a zm_ctx.  Arrays are (3, N) / (2, N) float64."""
 
     def __init__(self, n1, n2=None, L1=1.0, L2=1.0, periodic=True, atwood=0.5, g=1.0, mu=0.0,
-                 delta=None, order=ZM_ORDER_HIGH, fp32c=False, stream=None):
+                 delta=None, order=ZM_ORDER_HIGH, fp32c=False, df64=False, stream=None):
         self.n1 = int(n1)
         self.n2 = int(n1 if n2 is None else n2)
         self.N = self.n1 * self.n2
-        self.order = order | (ZM_PREC_FP32C if fp32c else 0)
+        self.order = order | (ZM_PREC_FP32C if fp32c else 0) | (ZM_PREC_DF64 if df64 else 0)
         self.h = zm_create(self.n1, self.n2, L1, L2, periodic, atwood, g, mu, delta, self.order)
         if stream is not None:
             zm_set_stream(self.h, stream)

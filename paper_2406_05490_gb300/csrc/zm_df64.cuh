@@ -132,5 +132,114 @@ __device__ __forceinline__ cdf cmul_pm_i(cdf a, int s)
     return s > 0 ? cdf{neg(a.im), a.re} : cdf{a.im, neg(a.re)};
 }
 
+// ---- complex double words in packed FP32x2 instructions ------------------------------------
+// One complex double word as two 64-bit registers: h = (re.hi, im.hi), l = (re.lo, im.lo); each
+// fma/mul/add/sub .f32x2 instruction applies the same FP32 operation to both lanes, so the real
+// and imaginary parts of an operation share one issue slot.  In memory: {re.hi, im.hi, re.lo,
+// im.lo} (16 bytes, read and written as ulonglong2).
+using u64 = unsigned long long;
+
+__device__ __forceinline__ u64 add2(u64 a, u64 b)
+{
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b)
+{
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b)
+{
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c)
+{
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+constexpr u64 kSign0 = 0x0000000080000000ull, kSign1 = 0x8000000000000000ull;
+__device__ __forceinline__ u64 neg2(u64 a) { return a ^ (kSign0 | kSign1); }
+__device__ __forceinline__ u64 pk(float x, float y)
+{
+    return (u64)__float_as_uint(x) | ((u64)__float_as_uint(y) << 32);
+}
+__device__ __forceinline__ float lane0(u64 a) { return __uint_as_float((unsigned)a); }
+__device__ __forceinline__ float lane1(u64 a) { return __uint_as_float((unsigned)(a >> 32)); }
+// (x, y) -> (-y, x)
+__device__ __forceinline__ u64 rot2(u64 a) { return pk(-lane1(a), lane0(a)); }
+
+struct C2 {
+    u64 h, l;
+};
+
+__device__ __forceinline__ C2 ld2(ulonglong2 v) { return C2{v.x, v.y}; }
+__device__ __forceinline__ ulonglong2 st2(C2 a) { return make_ulonglong2(a.h, a.l); }
+__device__ __forceinline__ C2 c2_from(df re, df im) { return C2{pk(re.hi, im.hi), pk(re.lo, im.lo)}; }
+__device__ __forceinline__ df c2_re(C2 a) { return df{lane0(a.h), lane0(a.l)}; }
+
+__device__ __forceinline__ void two_sum2(u64 a, u64 b, u64 &s, u64 &e)
+{
+    s = add2(a, b);
+    const u64 bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+// s + e == a - b exactly (two_sum of a and -b)
+__device__ __forceinline__ void two_diff2(u64 a, u64 b, u64 &s, u64 &e)
+{
+    s = sub2(a, b);
+    const u64 bb = sub2(s, a);
+    e = sub2(sub2(a, sub2(s, bb)), add2(b, bb));
+}
+__device__ __forceinline__ C2 fast_two_sum2(u64 a, u64 b)
+{
+    const u64 s = add2(a, b);
+    return C2{s, sub2(b, sub2(s, a))};
+}
+
+// sloppy double-word sums of both parts (11 packed instructions)
+__device__ __forceinline__ C2 cadd2(C2 x, C2 y)
+{
+    u64 s, e;
+    two_sum2(x.h, y.h, s, e);
+    return fast_two_sum2(s, add2(e, add2(x.l, y.l)));
+}
+__device__ __forceinline__ C2 csub2(C2 x, C2 y)
+{
+    u64 s, e;
+    two_diff2(x.h, y.h, s, e);
+    return fast_two_sum2(s, add2(e, sub2(x.l, y.l)));
+}
+
+// a * w = a wr + (-a.im, a.re) wi, both products exact in their leading parts (two_prod), summed
+// with one TwoSum and one renormalisation (19 packed instructions): normwise error a few u^2.
+__device__ __forceinline__ C2 cmul2(C2 a, C2 w)
+{
+    const u64 wrh = pk(lane0(w.h), lane0(w.h)), wrl = pk(lane0(w.l), lane0(w.l));
+    const u64 wih = pk(lane1(w.h), lane1(w.h)), wil = pk(lane1(w.l), lane1(w.l));
+    const u64 bh = rot2(a.h), bl = rot2(a.l);
+    const u64 p1 = mul2(a.h, wrh), p2 = mul2(bh, wih);
+    const u64 e1 = fma2(a.h, wrh, neg2(p1)), e2 = fma2(bh, wih, neg2(p2));
+    u64 s, e3;
+    two_sum2(p1, p2, s, e3);
+    u64 t = add2(e1, add2(e2, e3));
+    t = fma2(a.l, wrh, t);
+    t = fma2(a.h, wrl, t);
+    t = fma2(bl, wih, t);
+    t = fma2(bh, wil, t);
+    return fast_two_sum2(s, t);
+}
+
+// a * (+i) for s > 0, a * (-i) for s < 0 (exact)
+__device__ __forceinline__ C2 cmul_i2(C2 a, int s)
+{
+    return s > 0 ? C2{rot2(a.h), rot2(a.l)} : C2{neg2(rot2(a.h)), neg2(rot2(a.l))};
+}
+
 }  // namespace dw
 }  // namespace zm

@@ -14,6 +14,7 @@
 // Conversions between the FP64 API arrays and this storage run only at set/get/velocity calls.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "zm_df64.cuh"
 #include "zm_internal.cuh"
@@ -24,7 +25,6 @@ namespace {
 using namespace dw;
 
 constexpr int kTpb = 256;
-constexpr int kFftTpb = 256;
 
 // A double-word constant prepared on the host.
 struct Dc {
@@ -168,187 +168,331 @@ __global__ void __launch_bounds__(kTpb)
 // ---- FFT Riesz velocity --------------------------------------------------------------------------
 // The same three passes as the FP64 path (rows forward with a transposed write; columns
 // forward, Riesz multiplier, inverse, transposed write; rows inverse with the velocity
-// epilogue), on complex double words (float4) in shared memory.  Butterflies are radix-2^2:
-// two radix-2 stages fused into one radix-4 step with three twiddle products instead of
-// four, which keeps the bit-reversed order of plain radix-2 (one radix-2 stage when log2 L is
-// odd).  Twiddles W_L^k = exp(-2 pi i k / L) come from a half table (k < L/2), the upper
-// range by W_L^(k + L/2) = -W_L^k, conjugated for the inverse.
+// epilogue), on complex double words in packed FP32x2 instructions.
+//
+// Each pass holds `rows` complete rows (rows * L = 4096 complex values, 68 KiB with padding)
+// in shared memory.  The log2 L radix-2 stages are done in chunks of K <= 4 stages: a thread
+// loads a group of 2^K values spaced h apart into registers, applies the chunk's stages there
+// and writes the group back, so shared memory is traversed once per chunk rather than once per
+// stage.  Inside a chunk, pairs of stages are fused as radix-2^2 butterflies (three twiddle
+// products per four values instead of four, bit-reversed order kept).  The first chunk of a
+// pass reads its group straight from global memory; in pass B the last forward chunk, the
+// Riesz multiplier and the first inverse chunk share one register group (the forward
+// transform's last chunk and the inverse transform's first chunk both act on 2^K consecutive
+// bit-reversed positions).  Shared memory is padded by one entry per 16 so that groups of
+// consecutive values (h = 1) do not collide in banks.
+// Twiddles W_L^k = exp(-2 pi i k / L) come from a half table (k < L/2), the upper range by
+// W_L^(k + L/2) = -W_L^k, conjugated for the inverse.
+
+#ifndef ZM_DF_KMAX
+#define ZM_DF_KMAX 4  // most radix-2 stages per register group (group of 2^K values)
+#endif
+#ifndef ZM_DF_ELEMS
+#define ZM_DF_ELEMS 4096  // complex values per CTA of an FFT pass (rows * row length)
+#endif
+constexpr int kKmax = ZM_DF_KMAX;
+constexpr int kFftElems = ZM_DF_ELEMS;
 
 __device__ __forceinline__ int bitrev(int j, int logL) { return (int)(__brev((unsigned)j) >> (32 - logL)); }
+__device__ __forceinline__ int phys(int i) { return i + (i >> 4); }
 
-__device__ __forceinline__ cdf tw_get(const float4 *__restrict__ tw, int k, int half, int sgn)
+__device__ __forceinline__ C2 tw_get(const ulonglong2 *__restrict__ tw, int k, int half, int sgn)
 {
     const bool up = k >= half;
-    float4 v = __ldg(tw + (up ? k - half : k));
-    if (up) v = make_float4(-v.x, -v.y, -v.z, -v.w);
-    if (sgn > 0) {
-        v.z = -v.z;
-        v.w = -v.w;
-    }
-    return ld_c(v);
+    const ulonglong2 v = __ldg(tw + (up ? k - half : k));
+    u64 flip = up ? (kSign0 | kSign1) : 0ull;
+    if (sgn > 0) flip ^= kSign1;  // conjugate: negate the imaginary lane
+    return C2{v.x ^ flip, v.y ^ flip};
 }
 
-// Decimation in frequency on `rows` rows of length L = 2^logL: natural order in, bit-reversed
-// order out.  sgn = -1 forward, +1 inverse (unnormalised).
-__device__ void dif_df(float4 *x, int rows, int logL, const float4 *__restrict__ tw, int sgn)
+// Radix-2^2 decimation-in-frequency butterfly on v[m], v[m+Q], v[m+2Q], v[m+3Q] (positions
+// p, p + S, p + 2S, p + 3S of a block of 4S); e1 = exponent of W_{4S}^p on W_L.
+template <int Q>
+__device__ __forceinline__ void bfly_dif(C2 *v, int m, int e1, int half, const ulonglong2 *__restrict__ tw, int sgn)
 {
-    const int L = 1 << logL, half = L >> 1, quarter = L >> 2;
-    if (logL & 1) {
-        for (int b = threadIdx.x; b < rows * half; b += blockDim.x) {
-            const int row = b >> (logL - 1), pos = b & (half - 1);
-            float4 *xr = x + (row << logL);
-            const cdf u = ld_c(xr[pos]), v = ld_c(xr[pos + half]);
-            const cdf d = csub(u, v);
-            xr[pos] = st_c(cadd(u, v));
-            xr[pos + half] = st_c(pos ? cmul(d, tw_get(tw, pos, half, sgn)) : d);
-        }
-        __syncthreads();
-    }
-    for (int h = (logL & 1) ? (L >> 3) : (L >> 2); h >= 1; h >>= 2) {
-        const int lh = __ffs(h) - 1;
-        const int step = half / (2 * h);  // W_{4h}^m = W_L^(m * step)
-        for (int b = threadIdx.x; b < rows * quarter; b += blockDim.x) {
-            const int row = b >> (logL - 2), idx = b & (quarter - 1);
-            const int pos = idx & (h - 1);
-            float4 *xr = x + (row << logL) + ((idx >> lh) << (lh + 2)) + pos;
-            const cdf a0 = ld_c(xr[0]), a1 = ld_c(xr[h]), a2 = ld_c(xr[2 * h]), a3 = ld_c(xr[3 * h]);
-            const cdf s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3);
-            const cdf d13 = cmul_pm_i(csub(a1, a3), sgn);  // times W_{4h}^h = -+i
-            const cdf X0 = cadd(s02, s13), X2 = csub(s02, s13);
-            const cdf X1 = cadd(d02, d13), X3 = csub(d02, d13);
-            xr[0] = st_c(X0);
-            if (pos == 0) {
-                xr[h] = st_c(X2);
-                xr[2 * h] = st_c(X1);
-                xr[3 * h] = st_c(X3);
-            } else {
-                xr[h] = st_c(cmul(X2, tw_get(tw, 2 * pos * step, half, sgn)));
-                xr[2 * h] = st_c(cmul(X1, tw_get(tw, pos * step, half, sgn)));
-                xr[3 * h] = st_c(cmul(X3, tw_get(tw, 3 * pos * step, half, sgn)));
-            }
-        }
-        __syncthreads();
+    const C2 a0 = v[m], a1 = v[m + Q], a2 = v[m + 2 * Q], a3 = v[m + 3 * Q];
+    const C2 s02 = cadd2(a0, a2), d02 = csub2(a0, a2), s13 = cadd2(a1, a3);
+    const C2 d13 = cmul_i2(csub2(a1, a3), sgn);
+    v[m] = cadd2(s02, s13);
+    const C2 x2 = csub2(s02, s13), x1 = cadd2(d02, d13), x3 = csub2(d02, d13);
+    if (e1 == 0) {
+        v[m + Q] = x2;
+        v[m + 2 * Q] = x1;
+        v[m + 3 * Q] = x3;
+    } else {
+        v[m + Q] = cmul2(x2, tw_get(tw, 2 * e1, half, sgn));
+        v[m + 2 * Q] = cmul2(x1, tw_get(tw, e1, half, sgn));
+        v[m + 3 * Q] = cmul2(x3, tw_get(tw, 3 * e1, half, sgn));
     }
 }
 
-// Decimation in time: bit-reversed order in, natural order out.
-__device__ void dit_df(float4 *x, int rows, int logL, const float4 *__restrict__ tw, int sgn)
+// Radix-2^2 decimation-in-time butterfly (spans S, then 2S).
+template <int Q>
+__device__ __forceinline__ void bfly_dit(C2 *v, int m, int e1, int half, const ulonglong2 *__restrict__ tw, int sgn)
 {
-    const int L = 1 << logL, half = L >> 1, quarter = L >> 2;
-    for (int h = 1; 4 * h <= L; h <<= 2) {
-        const int lh = __ffs(h) - 1;
-        const int step = half / (2 * h);
-        for (int b = threadIdx.x; b < rows * quarter; b += blockDim.x) {
-            const int row = b >> (logL - 2), idx = b & (quarter - 1);
-            const int pos = idx & (h - 1);
-            float4 *xr = x + (row << logL) + ((idx >> lh) << (lh + 2)) + pos;
-            const cdf a0 = ld_c(xr[0]);
-            cdf c1 = ld_c(xr[h]), c2 = ld_c(xr[2 * h]), c3 = ld_c(xr[3 * h]);
-            if (pos) {
-                c1 = cmul(c1, tw_get(tw, 2 * pos * step, half, sgn));
-                c2 = cmul(c2, tw_get(tw, pos * step, half, sgn));
-                c3 = cmul(c3, tw_get(tw, 3 * pos * step, half, sgn));
-            }
-            const cdf s01 = cadd(a0, c1), d01 = csub(a0, c1), s23 = cadd(c2, c3);
-            const cdf d23 = cmul_pm_i(csub(c2, c3), sgn);
-            xr[0] = st_c(cadd(s01, s23));
-            xr[2 * h] = st_c(csub(s01, s23));
-            xr[h] = st_c(cadd(d01, d23));
-            xr[3 * h] = st_c(csub(d01, d23));
-        }
-        __syncthreads();
+    const C2 a0 = v[m];
+    C2 c1 = v[m + Q], c2 = v[m + 2 * Q], c3 = v[m + 3 * Q];
+    if (e1 != 0) {
+        c1 = cmul2(c1, tw_get(tw, 2 * e1, half, sgn));
+        c2 = cmul2(c2, tw_get(tw, e1, half, sgn));
+        c3 = cmul2(c3, tw_get(tw, 3 * e1, half, sgn));
     }
-    if (logL & 1) {
-        for (int b = threadIdx.x; b < rows * half; b += blockDim.x) {
-            const int row = b >> (logL - 1), pos = b & (half - 1);
-            float4 *xr = x + (row << logL);
-            const cdf u = ld_c(xr[pos]);
-            cdf v = ld_c(xr[pos + half]);
-            if (pos) v = cmul(v, tw_get(tw, pos, half, sgn));
-            xr[pos] = st_c(cadd(u, v));
-            xr[pos + half] = st_c(csub(u, v));
+    const C2 s01 = cadd2(a0, c1), d01 = csub2(a0, c1), s23 = cadd2(c2, c3);
+    const C2 d23 = cmul_i2(csub2(c2, c3), sgn);
+    v[m] = cadd2(s01, s23);
+    v[m + 2 * Q] = csub2(s01, s23);
+    v[m + Q] = cadd2(d01, d23);
+    v[m + 3 * Q] = csub2(d01, d23);
+}
+
+// The K decimation-in-frequency stages of one chunk on a register group: v[m] is the value at
+// position base + m h of its row (h = 2^lh, pos = base mod h); spans h 2^(K-1) down to h.
+template <int K>
+__device__ __forceinline__ void dif_chunk(C2 *v, int pos, int lh, int logL, const ulonglong2 *__restrict__ tw, int sgn)
+{
+    constexpr int R = 1 << K;
+    const int half = 1 << (logL - 1);
+    if (K & 1) {  // one radix-2 stage at the top span S = h 2^(K-1): W_{2S}^(pos + m h)
+#pragma unroll
+        for (int m = 0; m < R / 2; ++m) {
+            const C2 a = v[m], b = v[m + R / 2];
+            v[m] = cadd2(a, b);
+            const C2 d = csub2(a, b);
+            const int e = (pos + (m << lh)) << (logL - lh - K);
+            v[m + R / 2] = e ? cmul2(d, tw_get(tw, e, half, sgn)) : d;
         }
-        __syncthreads();
+    }
+#pragma unroll
+    for (int jj = (K & 1) ? K - 3 : K - 2; jj >= 0; jj -= 2) {  // spans (2S, S), S = h 2^jj
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            if ((m & (4 << jj) - 1) >= (1 << jj)) continue;  // quadruple leaders only
+            const int r = m & ((1 << jj) - 1);
+            const int e1 = (pos + (r << lh)) << (logL - lh - jj - 2);
+            if (jj == 0) bfly_dif<1>(v, m, e1, half, tw, sgn);
+            else bfly_dif<4>(v, m, e1, half, tw, sgn);
+        }
     }
 }
 
-// pass A: rows i (length n2) of c = w1 + i w2; forward; write out[j][i] (transposed).
-__global__ void __launch_bounds__(kFftTpb)
-    pass_a_df(int n1, int n2, int l2, int lr, const float2 *__restrict__ w,
-              const float4 *__restrict__ tw2, float4 *__restrict__ out)
+// The K decimation-in-time stages of one chunk: spans h up to h 2^(K-1).
+template <int K>
+__device__ __forceinline__ void dit_chunk(C2 *v, int pos, int lh, int logL, const ulonglong2 *__restrict__ tw, int sgn)
 {
-    extern __shared__ float4 sx[];
+    constexpr int R = 1 << K;
+    const int half = 1 << (logL - 1);
+#pragma unroll
+    for (int jj = 0; jj + 2 <= K; jj += 2) {  // spans (S, 2S), S = h 2^jj
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            if ((m & (4 << jj) - 1) >= (1 << jj)) continue;
+            const int r = m & ((1 << jj) - 1);
+            const int e1 = (pos + (r << lh)) << (logL - lh - jj - 2);
+            if (jj == 0) bfly_dit<1>(v, m, e1, half, tw, sgn);
+            else bfly_dit<4>(v, m, e1, half, tw, sgn);
+        }
+    }
+    if (K & 1) {  // one radix-2 stage at the top span
+#pragma unroll
+        for (int m = 0; m < R / 2; ++m) {
+            const C2 a = v[m];
+            C2 b = v[m + R / 2];
+            const int e = (pos + (m << lh)) << (logL - lh - K);
+            if (e) b = cmul2(b, tw_get(tw, e, half, sgn));
+            v[m] = cadd2(a, b);
+            v[m + R / 2] = csub2(a, b);
+        }
+    }
+}
+
+// Chunk plan, fixed at compile time per row length 2^l: ceil(l / kKmax) chunks of near-equal
+// size, the larger ones last (so that the last forward chunk of pass B, which the first inverse
+// chunk mirrors, is the largest).  Chunk c of the forward transform, and chunk c of the inverse
+// one, act on values spaced 2^lh_of(l, c) apart.
+constexpr int nc_of(int l) { return (l + kKmax - 1) / kKmax; }
+constexpr int k_of(int l, int c) { return l / nc_of(l) + (c >= nc_of(l) - l % nc_of(l) ? 1 : 0); }
+constexpr int lh_of(int l, int c) { return c < 0 ? l : lh_of(l, c - 1) - k_of(l, c); }
+
+// Group g of a chunk with 2^K values per group and spacing h = 2^lh, in a pass over `rows`
+// rows of length 2^l: its row, pos and base position.
+struct Grp {
+    int row, pos, base;
+};
+
+__device__ __forceinline__ Grp group_of(int g, int K, int lh, int l)
+{
+    const int per_row = 1 << (l - K);
+    const int gi = g & (per_row - 1);
+    const int pos = gi & ((1 << lh) - 1);
+    return Grp{g >> (l - K), pos, ((gi >> lh) << (lh + K)) + pos};
+}
+
+// One chunk: load each group with ld(row, index), run the K stages, store with st(row, index).
+template <int K, bool kDif, int L, int LH, class Ld, class St>
+__device__ __forceinline__ void chunk_pass(int rows, const ulonglong2 *__restrict__ tw, int sgn, Ld ld, St st)
+{
+    constexpr int R = 1 << K;
+    const int ngroups = rows << (L - K);
+    for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+        const Grp q = group_of(g, K, LH, L);
+        C2 v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = ld(q.row, q.base + (m << LH));
+        if (kDif) dif_chunk<K>(v, q.pos, LH, L, tw, sgn);
+        else dit_chunk<K>(v, q.pos, LH, L, tw, sgn);
+#pragma unroll
+        for (int m = 0; m < R; ++m) st(q.row, q.base + (m << LH), v[m]);
+    }
+}
+
+// Forward chunks C .. CEnd of `rows` rows of length 2^L in shared memory `sx` (padded); chunk 0
+// reads its groups with ld0 (global memory) instead.
+template <int L, int C, int CEnd, class Ld0>
+__device__ __forceinline__ void dif_seq(ulonglong2 *sx, const ulonglong2 *__restrict__ tw, int rows, int sgn, Ld0 ld0)
+{
+    if constexpr (C <= CEnd) {
+        constexpr int K = k_of(L, C), LH = lh_of(L, C);
+        auto sts = [&](int row, int i, C2 v) { sx[phys((row << L) + i)] = st2(v); };
+        if constexpr (C == 0) {
+            chunk_pass<K, true, L, LH>(rows, tw, sgn, ld0, sts);
+        } else {
+            auto lds = [&](int row, int i) { return ld2(sx[phys((row << L) + i)]); };
+            chunk_pass<K, true, L, LH>(rows, tw, sgn, lds, sts);
+        }
+        __syncthreads();
+        dif_seq<L, C + 1, CEnd>(sx, tw, rows, sgn, ld0);
+    }
+}
+
+// Inverse chunks C, C - 1, .., 0 (spans growing) in shared memory.
+template <int L, int C>
+__device__ __forceinline__ void dit_seq(ulonglong2 *sx, const ulonglong2 *__restrict__ tw, int rows, int sgn)
+{
+    if constexpr (C >= 0) {
+        constexpr int K = k_of(L, C), LH = lh_of(L, C);
+        auto lds = [&](int row, int i) { return ld2(sx[phys((row << L) + i)]); };
+        auto sts = [&](int row, int i, C2 v) { sx[phys((row << L) + i)] = st2(v); };
+        chunk_pass<K, false, L, LH>(rows, tw, sgn, lds, sts);
+        __syncthreads();
+        dit_seq<L, C - 1>(sx, tw, rows, sgn);
+    }
+}
+
+__device__ __forceinline__ ulonglong2 c2_pack(float2 re, float2 im)
+{
+    return make_ulonglong2(pk(re.x, im.x), pk(re.y, im.y));
+}
+
+// Threads per CTA and resident CTAs per SM of the passes over rows of length 2^L: one group of
+// 16 values per thread over the CTA's kFftElems values (a single row when it is longer), with the
+// register budget of 128 per thread that this occupancy leaves.
+constexpr int elems_for(int L) { return (1 << L) > kFftElems ? (1 << L) : kFftElems; }
+constexpr int threads_for(int L) { return elems_for(L) / 16; }
+constexpr int minb_for(int L) { return 65536 / (threads_for(L) * 128); }
+
+// pass A: rows i (length n2 = 2^L) of c = w1 + i w2; forward; write out[j][i] (transposed).
+template <int L>
+__global__ void __launch_bounds__(threads_for(L), minb_for(L))
+    pass_a_df(int n1, int lr, const float2 *__restrict__ w, const ulonglong2 *__restrict__ tw2,
+              ulonglong2 *__restrict__ out)
+{
+    extern __shared__ ulonglong2 sx[];
     const int rows = 1 << lr;
     const int i0 = blockIdx.x * rows;
-    const size_t N = (size_t)n1 * n2;
-    const size_t o = (size_t)i0 * n2;
-    for (int e = threadIdx.x; e < (rows << l2); e += blockDim.x) {
-        const float2 a = w[o + e], b = w[N + o + e];
-        sx[e] = make_float4(a.x, a.y, b.x, b.y);
-    }
-    __syncthreads();
-    dif_df(sx, rows, l2, tw2, -1);
-    for (int e = threadIdx.x; e < (rows << l2); e += blockDim.x) {
+    const size_t N = (size_t)n1 << L;
+    const float2 *w1 = w + ((size_t)i0 << L), *w2 = w1 + N;
+    auto ldg = [&](int row, int i) { return ld2(c2_pack(w1[(row << L) + i], w2[(row << L) + i])); };
+    dif_seq<L, 0, nc_of(L) - 1>(sx, tw2, rows, -1, ldg);
+    for (int e = threadIdx.x; e < (rows << L); e += blockDim.x) {
         const int j = e >> lr, r = e & (rows - 1);
-        out[(size_t)j * n1 + i0 + r] = sx[(r << l2) + bitrev(j, l2)];
+        out[(size_t)j * n1 + i0 + r] = sx[phys((r << L) + bitrev(j, L))];
     }
 }
 
-// pass B: rows j (length n1) of the transpose; forward; multiply by -(k2 + i k1)/|k| (zero at
-// k = 0 and on the Nyquist row and column); inverse; write out[i][j].  k_l / |k| is formed from
-// t_l = m_l / L_l (the 2 pi cancels).
-__global__ void __launch_bounds__(kFftTpb)
-    pass_b_df(int n1, int n2, int l1, int lr, Dc invL1, Dc invL2, const float4 *__restrict__ in,
-              const float4 *__restrict__ tw1, float4 *__restrict__ out)
+// The Riesz multiplier -(k2 + i k1)/|k| at frequency (i, j) as a complex double word, zero at
+// k = 0 and on the Nyquist row and column; k_l/|k| is formed from t_l = m_l / L_l (2 pi cancels).
+__device__ __forceinline__ C2 riesz_mult(int i, int j, int n1, int n2, Dc invL1, Dc invL2)
 {
-    extern __shared__ float4 sx[];
+    const int m1 = (i < n1 / 2) ? i : i - n1;
+    const int m2 = (j < n2 / 2) ? j : j - n2;
+    if ((m1 == 0 && m2 == 0) || 2 * i == n1 || 2 * j == n2) return C2{0ull, 0ull};
+    const df t1 = mul_f(dc(invL1), (float)m1), t2 = mul_f(dc(invL2), (float)m2);
+    const df rs = rsqrt(add(sqr(t1), sqr(t2)));
+    return c2_from(neg(mul(t2, rs)), neg(mul(t1, rs)));
+}
+
+// Pass B's middle: the last forward chunk, the multiplier and the first inverse chunk on one
+// register group of 2^K consecutive (bit-reversed) positions of a column of length 2^L.
+template <int L>
+__device__ __forceinline__ void mid_b(ulonglong2 *sx, int rows, int j0, int n2, Dc invL1, Dc invL2,
+                                      const ulonglong2 *__restrict__ tw1)
+{
+    constexpr int K = k_of(L, nc_of(L) - 1), R = 1 << K;
+    const int ngroups = rows << (L - K);
+    for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+        const Grp q = group_of(g, K, 0, L);
+        C2 v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = ld2(sx[phys((q.row << L) + q.base + m)]);
+        dif_chunk<K>(v, 0, 0, L, tw1, -1);
+        const int ib = bitrev(q.base, L);
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const int i = ib | (bitrev(m, K) << (L - K));  // natural frequency index of base + m
+            v[m] = cmul2(v[m], riesz_mult(i, j0 + q.row, 1 << L, n2, invL1, invL2));
+        }
+        dit_chunk<K>(v, 0, 0, L, tw1, +1);
+#pragma unroll
+        for (int m = 0; m < R; ++m) sx[phys((q.row << L) + q.base + m)] = st2(v[m]);
+    }
+}
+
+// pass B: rows j (length n1 = 2^L) of the transpose; forward; multiply; inverse; write out[i][j].
+template <int L>
+__global__ void __launch_bounds__(threads_for(L), minb_for(L))
+    pass_b_df(int n2, int lr, Dc invL1, Dc invL2, const ulonglong2 *__restrict__ in,
+              const ulonglong2 *__restrict__ tw1, ulonglong2 *__restrict__ out)
+{
+    extern __shared__ ulonglong2 sx[];
+    constexpr int NC = nc_of(L);
     const int rows = 1 << lr;
     const int j0 = blockIdx.x * rows;
-    const float4 *src = in + ((size_t)j0 << l1);
-    for (int e = threadIdx.x; e < (rows << l1); e += blockDim.x) sx[e] = src[e];
-    __syncthreads();
-    dif_df(sx, rows, l1, tw1, -1);
-    for (int e = threadIdx.x; e < (rows << l1); e += blockDim.x) {
-        const int r = e >> l1, pos = e & (n1 - 1);
-        const int i = bitrev(pos, l1), j = j0 + r;
-        const int m1 = (i < n1 / 2) ? i : i - n1;
-        const int m2 = (j < n2 / 2) ? j : j - n2;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (!(m1 == 0 && m2 == 0) && 2 * i != n1 && 2 * j != n2) {
-            const df t1 = mul_f(dc(invL1), (float)m1), t2 = mul_f(dc(invL2), (float)m2);
-            const df rs = rsqrt(add(sqr(t1), sqr(t2)));
-            const cdf mult{neg(mul(t2, rs)), neg(mul(t1, rs))};
-            v = st_c(cmul(ld_c(sx[e]), mult));
-        }
-        sx[e] = v;
+    const ulonglong2 *src = in + ((size_t)j0 << L);
+    if constexpr (NC == 1) {  // the whole transform is the middle group: stage the rows first
+        for (int e = threadIdx.x; e < (rows << L); e += blockDim.x) sx[phys(e)] = src[e];
+        __syncthreads();
+    } else {
+        auto ldg = [&](int row, int i) { return ld2(src[(row << L) + i]); };
+        dif_seq<L, 0, NC - 2>(sx, tw1, rows, -1, ldg);
     }
+    mid_b<L>(sx, rows, j0, n2, invL1, invL2, tw1);
     __syncthreads();
-    dit_df(sx, rows, l1, tw1, +1);
-    for (int e = threadIdx.x; e < (rows << l1); e += blockDim.x) {
+    dit_seq<L, NC - 2>(sx, tw1, rows, +1);
+    for (int e = threadIdx.x; e < (rows << L); e += blockDim.x) {
         const int i = e >> lr, r = e & (rows - 1);
-        out[(size_t)i * n2 + j0 + r] = sx[(r << l1) + i];
+        out[(size_t)i * n2 + j0 + r] = sx[phys((r << L) + i)];
     }
 }
 
-// pass C: rows i (length n2); inverse; s = Re / (n1 n2); u = -s/2 N; Phi = q + |u|^2 / 2.
-__global__ void __launch_bounds__(kFftTpb)
-    pass_c_df(int n1, int n2, int l2, int lr, float scale, const float4 *__restrict__ in,
-              const float4 *__restrict__ tw2, const float2 *__restrict__ nrm,
+// pass C: rows i (length n2 = 2^L); inverse; s = Re / (n1 n2); u = -s/2 N; Phi = q + |u|^2 / 2.
+template <int L>
+__global__ void __launch_bounds__(threads_for(L), minb_for(L))
+    pass_c_df(int n1, int lr, float scale, const ulonglong2 *__restrict__ in,
+              const ulonglong2 *__restrict__ tw2, const float2 *__restrict__ nrm,
               const float2 *__restrict__ q, float2 *__restrict__ u, float2 *__restrict__ phi)
 {
-    extern __shared__ float4 sx[];
+    extern __shared__ ulonglong2 sx[];
     const int rows = 1 << lr;
     const int i0 = blockIdx.x * rows;
-    const size_t N = (size_t)n1 * n2;
-    const size_t o = (size_t)i0 * n2;
-    for (int e = threadIdx.x; e < (rows << l2); e += blockDim.x) sx[e] = in[o + e];
-    __syncthreads();
-    dif_df(sx, rows, l2, tw2, +1);
-    for (int e = threadIdx.x; e < (rows << l2); e += blockDim.x) {
-        const int r = e >> l2, j = e & (n2 - 1);
+    const size_t N = (size_t)n1 << L;
+    const size_t o = (size_t)i0 << L;
+    const ulonglong2 *src = in + o;
+    auto ldg = [&](int row, int i) { return ld2(src[(row << L) + i]); };
+    dif_seq<L, 0, nc_of(L) - 1>(sx, tw2, rows, +1, ldg);
+    for (int e = threadIdx.x; e < (rows << L); e += blockDim.x) {
+        const int r = e >> L, j = e & ((1 << L) - 1);
         const size_t p = o + e;
-        const float4 v = sx[(r << l2) + bitrev(j, l2)];
-        const df s = scale2(df{v.x, v.y}, scale);  // scale = -1 / (2 n1 n2), a power of two
+        const df s = scale2(c2_re(ld2(sx[phys((r << L) + bitrev(j, L))])), scale);  // scale = -1/(2 n1 n2)
         const df ux = mul(s, ldf(nrm, p)), uy = mul(s, ldf(nrm, N + p)), uz = mul(s, ldf(nrm, 2 * N + p));
         u[p] = to_f2(ux);
         u[N + p] = to_f2(uy);
@@ -358,6 +502,7 @@ __global__ void __launch_bounds__(kFftTpb)
     }
 }
 
+// twiddle table entry k < L/2: {cos.hi, sin.hi, cos.lo, sin.lo} of -2 pi k / L
 __global__ void twiddle_df_kernel(int L, float4 *tw)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -365,7 +510,7 @@ __global__ void twiddle_df_kernel(int L, float4 *tw)
     double s, c;
     sincospi(-2.0 * (double)k / (double)L, &s, &c);
     const float ch = __double2float_rn(c), sh = __double2float_rn(s);
-    tw[k] = make_float4(ch, __double2float_rn(c - (double)ch), sh, __double2float_rn(s - (double)sh));
+    tw[k] = make_float4(ch, sh, __double2float_rn(c - (double)ch), __double2float_rn(s - (double)sh));
 }
 
 // ---- conversions between the FP64 API arrays and double-word storage -----------------------------
@@ -412,6 +557,9 @@ __global__ void finite_f32_kernel(size_t n, const float *__restrict__ y, int *ba
         }
 }
 
+// padded shared-memory entries for `count` complex values (one pad entry per 16)
+int phys_host(int count) { return count + count / 16; }
+
 int ilog2(int n)
 {
     int l = 0;
@@ -419,8 +567,28 @@ int ilog2(int n)
     return l;
 }
 
-// rows per CTA of an FFT pass: rows * L * 16 bytes <= 64 KiB
-int lrows_for(int L) { return ilog2(std::max(1, std::min(8, 4096 / L))); }
+// log2 of the rows per CTA of an FFT pass over rows of length 2^l, and no more rows than the
+// pass has (`avail`).
+int lrows_for(int l, int avail) { return ilog2(std::max(1, std::min(elems_for(l) >> l, avail))); }
+
+// Calls f(std::integral_constant<int, l>) for the row-length exponents the FFT supports.
+template <class F>
+int with_log2(int l, F &&f)
+{
+    switch (l) {
+    case 3: return f(std::integral_constant<int, 3>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 5: return f(std::integral_constant<int, 5>{});
+    case 6: return f(std::integral_constant<int, 6>{});
+    case 7: return f(std::integral_constant<int, 7>{});
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 9: return f(std::integral_constant<int, 9>{});
+    case 10: return f(std::integral_constant<int, 10>{});
+    case 11: return f(std::integral_constant<int, 11>{});
+    case 12: return f(std::integral_constant<int, 12>{});
+    default: return set_error(ZM_ERR_UNSUPPORTED, "double-word FFT: side must be 2^3 .. 2^12");
+    }
+}
 
 DfGeo make_geo(const zm_ctx *c)
 {
@@ -442,8 +610,42 @@ DfGeo make_geo(const zm_ctx *c)
 
 inline const float2 *F2(const double *p) { return reinterpret_cast<const float2 *>(p); }
 inline float2 *F2(double *p) { return reinterpret_cast<float2 *>(p); }
-inline const float4 *F4(const double2 *p) { return reinterpret_cast<const float4 *>(p); }
-inline float4 *F4(double2 *p) { return reinterpret_cast<float4 *>(p); }
+inline const ulonglong2 *U2(const double2 *p) { return reinterpret_cast<const ulonglong2 *>(p); }
+inline ulonglong2 *U2(double2 *p) { return reinterpret_cast<ulonglong2 *>(p); }
+
+// Launches of the three passes for rows of length 2^L.  Each sets the kernel's dynamic shared
+// memory limit (a host-side attribute, legal during stream capture) and checks its own launch.
+template <int L>
+struct FftLaunch {
+    static int prep(const void *fn, size_t smem)
+    {
+        return cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                          "double-word FFT shared-memory attribute");
+    }
+    static int a(int n1, int lr, size_t smem, cudaStream_t s, const float2 *w, const ulonglong2 *tw2, ulonglong2 *out)
+    {
+        int rc = prep((const void *)pass_a_df<L>, smem);
+        if (rc) return rc;
+        pass_a_df<L><<<n1 >> lr, threads_for(L), smem, s>>>(n1, lr, w, tw2, out);
+        return cuda_check(cudaGetLastError(), "double-word FFT pass A launch");
+    }
+    static int b(int n2, int lr, size_t smem, cudaStream_t s, Dc invL1, Dc invL2, const ulonglong2 *in,
+                 const ulonglong2 *tw1, ulonglong2 *out)
+    {
+        int rc = prep((const void *)pass_b_df<L>, smem);
+        if (rc) return rc;
+        pass_b_df<L><<<n2 >> lr, threads_for(L), smem, s>>>(n2, lr, invL1, invL2, in, tw1, out);
+        return cuda_check(cudaGetLastError(), "double-word FFT pass B launch");
+    }
+    static int c(int n1, int lr, size_t smem, cudaStream_t s, float scale, const ulonglong2 *in,
+                 const ulonglong2 *tw2, const float2 *nrm, const float2 *q, float2 *u, float2 *phi)
+    {
+        int rc = prep((const void *)pass_c_df<L>, smem);
+        if (rc) return rc;
+        pass_c_df<L><<<n1 >> lr, threads_for(L), smem, s>>>(n1, lr, scale, in, tw2, nrm, q, u, phi);
+        return cuda_check(cudaGetLastError(), "double-word FFT pass C launch");
+    }
+};
 
 }  // namespace
 
@@ -458,15 +660,9 @@ int df_setup(zm_ctx *c)
         cudaGetLastError();
         return set_error(ZM_ERR_NOMEM, "df_setup: device allocation failed");
     }
-    twiddle_df_kernel<<<(g.n1 / 2 + 255) / 256, 256>>>(g.n1, F4(c->tw1));
-    twiddle_df_kernel<<<(g.n2 / 2 + 255) / 256, 256>>>(g.n2, F4(c->tw2));
-    const int smax = 64 * 1024;
-    int rc = cuda_check(cudaFuncSetAttribute(pass_a_df, cudaFuncAttributeMaxDynamicSharedMemorySize, smax),
-                        "df fft smem attribute");
-    if (!rc) rc = cuda_check(cudaFuncSetAttribute(pass_b_df, cudaFuncAttributeMaxDynamicSharedMemorySize, smax),
-                             "df fft smem attribute");
-    if (!rc) rc = cuda_check(cudaFuncSetAttribute(pass_c_df, cudaFuncAttributeMaxDynamicSharedMemorySize, smax),
-                             "df fft smem attribute");
+    twiddle_df_kernel<<<(g.n1 / 2 + 255) / 256, 256>>>(g.n1, reinterpret_cast<float4 *>(c->tw1));
+    twiddle_df_kernel<<<(g.n2 / 2 + 255) / 256, 256>>>(g.n2, reinterpret_cast<float4 *>(c->tw2));
+    int rc = ZM_OK;
     if (!rc) rc = cuda_check(cudaGetLastError(), "df twiddle kernel");
     return rc;
 }
@@ -485,17 +681,26 @@ int df_derivative(zm_ctx *c, const double *y)
     if (rc) return rc;
 
     const int l1 = ilog2(G.n1), l2 = ilog2(G.n2);
-    const int ra = lrows_for(G.n2), rb = lrows_for(G.n1);
-    prof_begin(c, ZM_K_FFT, &ev);
-    pass_a_df<<<G.n1 >> ra, kFftTpb, (G.n2 << ra) * sizeof(float4), c->stream>>>(
-        G.n1, G.n2, l2, ra, F2(y) + 3 * (size_t)G.N, F4(c->tw2), F4(c->fa));
-    pass_b_df<<<G.n2 >> rb, kFftTpb, (G.n1 << rb) * sizeof(float4), c->stream>>>(
-        G.n1, G.n2, l1, rb, split(1.0 / G.L1), split(1.0 / G.L2), F4(c->fa), F4(c->tw1), F4(c->fb));
+    const int ra = lrows_for(l2, G.n1), rb = lrows_for(l1, G.n2);
+    const size_t sa = (size_t)phys_host(G.n2 << ra) * sizeof(ulonglong2);
+    const size_t sb = (size_t)phys_host(G.n1 << rb) * sizeof(ulonglong2);
     const float scale = (float)(-0.5 / ((double)G.n1 * (double)G.n2));
-    pass_c_df<<<G.n1 >> ra, kFftTpb, (G.n2 << ra) * sizeof(float4), c->stream>>>(
-        G.n1, G.n2, l2, ra, scale, F4(c->fb), F4(c->tw2), F2(c->nrm), F2(c->q), F2(c->u), F2(c->phi));
+    prof_begin(c, ZM_K_FFT, &ev);
+    rc = with_log2(l2, [&](auto lc) {
+        return FftLaunch<decltype(lc)::value>::a(G.n1, ra, sa, c->stream, F2(y) + 3 * (size_t)G.N, U2(c->tw2),
+                                                 U2(c->fa));
+    });
+    if (!rc) rc = with_log2(l1, [&](auto lc) {
+        return FftLaunch<decltype(lc)::value>::b(G.n2, rb, sb, c->stream, split(1.0 / G.L1), split(1.0 / G.L2),
+                                                 U2(c->fa), U2(c->tw1), U2(c->fb));
+    });
+    if (!rc) rc = with_log2(l2, [&](auto lc) {
+        return FftLaunch<decltype(lc)::value>::c(G.n1, ra, sa, c->stream, scale, U2(c->fb), U2(c->tw2), F2(c->nrm),
+                                                 F2(c->q), F2(c->u), F2(c->phi));
+    });
     prof_end(c, ZM_K_FFT, ev);
     c->prof.acc.launches[ZM_K_FFT] += 2;  // three kernels per Riesz evaluation
+    if (rc) return rc;
     return cuda_check(cudaGetLastError(), "double-word Riesz launch");
 }
 

@@ -535,9 +535,17 @@ def run_gb300(args):
         k64 = 2
         ms64, prof64 = timed_steps(m64, zm, torch, k64, 1, flush)
         m64.close()
+        # its all-pairs kernel against the FP64 FMA rate measured on this GPU by a probe kernel
+        br64_ms = prof64["ms"]["br"] / max(prof64["launches"]["br"], 1)
+        fp64_ach = FLOPS_PER_PAIR * N * N / (br64_ms * 1e-3) / 1e12
+        fp64_peak = zm.zm_measure_peak(zm.PEAK_FP64) / 1e12
         extras["fp64_plain"] = {"gpairs_per_s": pairs_per_step * k64 / (ms64 * 1e-3) / 1e9,
                                 "steps_per_s": k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64,
-                                "steps": k64}
+                                "steps": k64,
+                                "roofline": {"bound": "fp64 alu", "achieved": fp64_ach, "peak": fp64_peak,
+                                             "unit": "TFLOP/s", "frac": fp64_ach / fp64_peak,
+                                             "peak_basis": "measured FP64 FMA probe (zm_measure_peak)",
+                                             "flops_per_pair": FLOPS_PER_PAIR, "br_ms_per_launch": br64_ms}}
         extras["fp32c_speedup_vs_fp64"] = value / ws / extras["fp64_plain"]["gpairs_per_s"]
         # low order (FFT Riesz velocity): 1024^2 (the low-vs-high configuration), FP64 and
         # double-word; 4096^2, the largest power-of-two side below the paper's 4864^2 mesh

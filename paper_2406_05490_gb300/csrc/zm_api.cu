@@ -270,8 +270,7 @@ int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double de
     G.N = mesh->n1 * mesh->n2;
     G.L1 = mesh->L1;
     G.L2 = mesh->L2;
-    G.dx1 = mesh->L1 / mesh->n1;
-    G.dx2 = mesh->L2 / mesh->n2;
+    geom_finish(G);
     G.periodic = mesh->periodic ? 1 : 0;
     const size_t N = G.N;
 

@@ -132,8 +132,7 @@ int Batch::alloc_inst(Inst &I, const zm_mesh &m, double atwood, double g, double
     I.geom.N = m.n1 * m.n2;
     I.geom.L1 = m.L1;
     I.geom.L2 = m.L2;
-    I.geom.dx1 = m.L1 / m.n1;
-    I.geom.dx2 = m.L2 / m.n2;
+    geom_finish(I.geom);
     I.geom.periodic = m.periodic ? 1 : 0;
     I.tiling = make_tiling(I.geom);
     I.atwood = atwood;

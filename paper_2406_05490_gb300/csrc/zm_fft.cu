@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kFftTpb)
 
 // pass B: rows j (length n1) of the transpose; forward; multiply; inverse; write out[i][j].
 __global__ void __launch_bounds__(kFftTpb)
-    pass_b(int n1, int n2, int log2n1, int rows, double L1, double L2,
+    pass_b(int n1, int n2, int log2n1, int rows, double invL1, double invL2,
            const double2 *__restrict__ in, const double2 *__restrict__ tw1, double2 *__restrict__ out)
 {
     extern __shared__ double2 sx[];
@@ -105,7 +105,6 @@ __global__ void __launch_bounds__(kFftTpb)
     for (int e = threadIdx.x; e < rows * n1; e += blockDim.x) sx[e] = in[(size_t)j0 * n1 + e];
     __syncthreads();
     fft_dif(sx, rows, n1, tw1, -1);
-    const double two_pi = 6.283185307179586476925286766559;
     for (int e = threadIdx.x; e < rows * n1; e += blockDim.x) {
         const int r = e / n1, pos = e - r * n1;
         const int i = bitrev(pos, log2n1), j = j0 + r;  // frequency indices
@@ -113,8 +112,9 @@ __global__ void __launch_bounds__(kFftTpb)
         const int m2 = (j < n2 / 2) ? j : j - n2;
         double2 v = make_double2(0.0, 0.0);
         if (!(m1 == 0 && m2 == 0) && 2 * i != n1 && 2 * j != n2) {
-            const double k1 = two_pi * m1 / L1, k2 = two_pi * m2 / L2;
-            const double ik = 1.0 / sqrt(k1 * k1 + k2 * k2);
+            // k_l / |k| with k_l = 2 pi m_l / L_l: the 2 pi cancels, t_l = m_l / L_l
+            const double k1 = m1 * invL1, k2 = m2 * invL2;
+            const double ik = dev::rsqrt_nr(k1 * k1 + k2 * k2);
             // multiplier -(k2 + i k1) / |k|
             v = cmul(sx[e], make_double2(-k2 * ik, -k1 * ik));
         }
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kFftTpb)
 
 // pass C: rows i (length n2); inverse; s = Re / (n1 n2); u = -s/2 N; Phi = q + |u|^2 / 2.
 __global__ void __launch_bounds__(kFftTpb)
-    pass_c(int n1, int n2, int log2n2, int rows, const double2 *__restrict__ in,
+    pass_c(int n1, int n2, int log2n2, int rows, double inv, const double2 *__restrict__ in,
            const double2 *__restrict__ tw2, const double *__restrict__ nrm,
            const double *__restrict__ q, double *__restrict__ u, double *__restrict__ phi)
 {
@@ -140,7 +140,6 @@ __global__ void __launch_bounds__(kFftTpb)
     for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) sx[e] = in[(size_t)i0 * n2 + e];
     __syncthreads();
     fft_dif(sx, rows, n2, tw2, +1);
-    const double inv = 1.0 / ((double)n1 * (double)n2);
     for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
         const int r = e / n2, j = e - r * n2;
         const size_t p = (size_t)(i0 + r) * n2 + j;
@@ -210,9 +209,9 @@ int launch_riesz(zm_ctx *c, const double *y)
     pass_a<<<g.n1 / ra, kFftTpb, ra * g.n2 * sizeof(double2), c->stream>>>(g.n1, g.n2, l2, ra, w,
                                                                             c->tw2, c->fa);
     pass_b<<<g.n2 / rb, kFftTpb, rb * g.n1 * sizeof(double2), c->stream>>>(
-        g.n1, g.n2, l1, rb, g.L1, g.L2, c->fa, c->tw1, c->fb);
+        g.n1, g.n2, l1, rb, 1.0 / g.L1, 1.0 / g.L2, c->fa, c->tw1, c->fb);
     pass_c<<<g.n1 / ra, kFftTpb, ra * g.n2 * sizeof(double2), c->stream>>>(
-        g.n1, g.n2, l2, ra, c->fb, c->tw2, c->nrm, c->q, c->u, c->phi);
+        g.n1, g.n2, l2, ra, 1.0 / ((double)g.n1 * (double)g.n2), c->fb, c->tw2, c->nrm, c->q, c->u, c->phi);
     prof_end(c, ZM_K_FFT, ev);
     c->prof.acc.launches[ZM_K_FFT] += 2;  // three kernels per Riesz evaluation
     return cuda_check(cudaGetLastError(), "Riesz FFT launch");

@@ -17,7 +17,22 @@ struct Geom {
     int n1, n2, N;
     double dx1, dx2, L1, L2;
     int periodic;
+    double i12a, i12b;    // 1 / (12 dx1), 1 / (12 dx2): first-difference weights
+    double i12a2, i12b2;  // 1 / (12 dx1^2), 1 / (12 dx2^2): second-difference weights
 };
+
+// Fill in the spacings and stencil weights of a Geom whose n1, n2, L1, L2 are set (on the host,
+// so that no kernel divides per node).
+inline void geom_finish(Geom &g)
+{
+    g.N = g.n1 * g.n2;
+    g.dx1 = g.L1 / g.n1;
+    g.dx2 = g.L2 / g.n2;
+    g.i12a = 1.0 / (12.0 * g.dx1);
+    g.i12b = 1.0 / (12.0 * g.dx2);
+    g.i12a2 = 1.0 / (12.0 * g.dx1 * g.dx1);
+    g.i12b2 = 1.0 / (12.0 * g.dx2 * g.dx2);
+}
 
 // Source records of the Birkhoff-Rott sum are stored tile-major: a tile is a tp1 x tp2 patch of
 // the mesh (compact in space for a smooth interface), ts = tp1 * tp2 slots, padded with
@@ -257,6 +272,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     for (uint32_t it = 0; it < kSpinLimit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// 1 / sqrt(x) for a positive double inside the FP32 range: the FP32 estimate refined by two
+// Newton-Raphson steps y <- y (3/2 - x/2 y^2) (relative error ~2^-22 -> ~2^-43 -> FP64 rounding),
+// a few FP64 instructions instead of a correctly rounded square root and division.
+__device__ __forceinline__ double rsqrt_nr(double x)
+{
+    const double hx = 0.5 * x;
+    double y = (double)rsqrtf((float)x);
+    y = y * fma(-hx * y, y, 1.5);
+    y = y * fma(-hx * y, y, 1.5);
+    return y;
 }
 
 __device__ __forceinline__ float rsqrt_approx(float x)

@@ -45,6 +45,8 @@ struct DfGeo {
     int N;
     Dc i12a, i12b;    // 1 / (12 dx1), 1 / (12 dx2)
     Dc i12a2, i12b2;  // 1 / (12 dx1^2), 1 / (12 dx2^2)
+    Dc d12a, d12b;    // 12 dx1, 12 dx2
+    Dc c8det;         // (144 dx1 dx2)^2 / 8
     Dc grav;          // g
     Dc m2a;           // -2 A
     Dc mu;
@@ -70,12 +72,18 @@ __device__ __forceinline__ Nb nb_axis1(int i, int j, const DfGeo &g)
     return Nb{r + ((j - 2) & m), r + ((j - 1) & m), r + ((j + 1) & m), r + ((j + 2) & m)};
 }
 
-// ((f-2 - f+2) + 8 (f+1 - f-1)) / (12 dx)
-__device__ __forceinline__ df diff1_df(const float2 *__restrict__ f, const Nb &n, df inv12)
+// (f-2 - f+2) + 8 (f+1 - f-1): 12 dx times the 4th-order first difference
+__device__ __forceinline__ df diff1_s(const float2 *__restrict__ f, const Nb &n)
 {
     const df a = sub(ldf(f, n.m2), ldf(f, n.p2));
     const df b = sub(ldf(f, n.p1), ldf(f, n.m1));
-    return mul(add(a, scale2(b, 8.0f)), inv12);
+    return add(a, scale2(b, 8.0f));
+}
+
+// ((f-2 - f+2) + 8 (f+1 - f-1)) / (12 dx)
+__device__ __forceinline__ df diff1_df(const float2 *__restrict__ f, const Nb &n, df inv12)
+{
+    return mul(diff1_s(f, n), inv12);
 }
 
 // (16 (f-1 + f+1) - (f-2 + f+2) - 30 f0) / (12 dx^2), accurate sums: the three groups cancel
@@ -88,8 +96,11 @@ __device__ __forceinline__ df diff2_df(const float2 *__restrict__ f, const Nb &n
     return mul(t, inv12sq);
 }
 
-// Geometry pass: unit normal N = a1 x a2 / |a1 x a2| and q = g z3 + 1/8 w^T h^-1 w, using
-// |a1 x a2|^2 = h11 h22 - h12^2 = det (Lagrange's identity) and 1/det = rsqrt(det)^2.
+// Geometry pass: unit normal N = a1 x a2 / |a1 x a2| and q = g z3 + 1/8 w^T h^-1 w.
+// The tangents are kept scaled, b_l = 12 dx_l a_l (the stencil sums without the division), since
+// the unit normal does not depend on their lengths; with gamma = w1 a2 - w2 a1 (formed from b and
+// w_l / (12 dx)), w^T h^-1 w = |gamma|^2 / det and det = |a1 x a2|^2 = |b1 x b2|^2 / (144 dx1 dx2)^2
+// (Lagrange's identity), so one rsqrt of |b1 x b2|^2 serves both.
 __global__ void __launch_bounds__(kTpb)
     geometry_df(DfGeo g, const float2 *__restrict__ y, float2 *__restrict__ q, float2 *__restrict__ nrm)
 {
@@ -98,31 +109,30 @@ __global__ void __launch_bounds__(kTpb)
     const int i = p >> g.l2, j = p & (g.n2 - 1);
     const size_t N = g.N;
     const Nb na = nb_axis0(i, j, g), nb = nb_axis1(i, j, g);
-    const df ia = dc(g.i12a), ib = dc(g.i12b);
-    df a1[3], a2[3];
+    df b1[3], b2[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        a1[c] = diff1_df(y + c * N, na, ia);
-        a2[c] = diff1_df(y + c * N, nb, ib);
+        b1[c] = diff1_s(y + c * N, na);
+        b2[c] = diff1_s(y + c * N, nb);
     }
-    a1[0] = add(from_f(1.0f), a1[0]);
-    a2[1] = add(from_f(1.0f), a2[1]);
-    const df nx = sub(mul(a1[1], a2[2]), mul(a1[2], a2[1]));
-    const df ny = sub(mul(a1[2], a2[0]), mul(a1[0], a2[2]));
-    const df nz = sub(mul(a1[0], a2[1]), mul(a1[1], a2[0]));
-    const df det = add(add(sqr(nx), sqr(ny)), sqr(nz));
-    const df rs = rsqrt(det);
+    b1[0] = add(dc(g.d12a), b1[0]);  // the mesh coordinate's share: 12 dx1 along alpha1
+    b2[1] = add(dc(g.d12b), b2[1]);
+    const df nx = sub(mul(b1[1], b2[2]), mul(b1[2], b2[1]));
+    const df ny = sub(mul(b1[2], b2[0]), mul(b1[0], b2[2]));
+    const df nz = sub(mul(b1[0], b2[1]), mul(b1[1], b2[0]));
+    const df rs = rsqrt(add(add(sqr(nx), sqr(ny)), sqr(nz)));
     nrm[p] = to_f2(mul(nx, rs));
     nrm[N + p] = to_f2(mul(ny, rs));
     nrm[2 * N + p] = to_f2(mul(nz, rs));
 
-    const df h11 = add(add(sqr(a1[0]), sqr(a1[1])), sqr(a1[2]));
-    const df h22 = add(add(sqr(a2[0]), sqr(a2[1])), sqr(a2[2]));
-    const df h12 = add(add(mul(a1[0], a2[0]), mul(a1[1], a2[1])), mul(a1[2], a2[2]));
-    const df w1 = ldf(y, 3 * N + p), w2 = ldf(y, 4 * N + p);
-    // h22 w1^2 - 2 h12 w1 w2 + h11 w2^2
-    const df t = add(sub(mul(h22, sqr(w1)), scale2(mul(h12, mul(w1, w2)), 2.0f)), mul(h11, sqr(w2)));
-    const df jump = scale2(mul(t, sqr(rs)), 0.125f);
+    // gamma = (w1 / (12 dx2)) b2 - (w2 / (12 dx1)) b1
+    const df s1 = mul(ldf(y, 3 * N + p), dc(g.i12b)), s2 = mul(ldf(y, 4 * N + p), dc(g.i12a));
+    const df gx = sub(mul(s1, b2[0]), mul(s2, b1[0]));
+    const df gy = sub(mul(s1, b2[1]), mul(s2, b1[1]));
+    const df gz = sub(mul(s1, b2[2]), mul(s2, b1[2]));
+    const df g2 = add(add(sqr(gx), sqr(gy)), sqr(gz));
+    // 1/8 |gamma|^2 / det = 1/8 |gamma|^2 rs^2 (144 dx1 dx2)^2
+    const df jump = mul(mul(g2, sqr(rs)), dc(g.c8det));
     q[p] = to_f2(add(mul(dc(g.grav), ldf(y, 2 * N + p)), jump));
 }
 
@@ -489,6 +499,7 @@ __global__ void __launch_bounds__(threads_for(L), minb_for(L))
     const ulonglong2 *src = in + o;
     auto ldg = [&](int row, int i) { return ld2(src[(row << L) + i]); };
     dif_seq<L, 0, nc_of(L) - 1>(sx, tw2, rows, +1, ldg);
+#pragma unroll 4
     for (int e = threadIdx.x; e < (rows << L); e += blockDim.x) {
         const int r = e >> L, j = e & ((1 << L) - 1);
         const size_t p = o + e;
@@ -602,6 +613,9 @@ DfGeo make_geo(const zm_ctx *c)
     g.i12b = split(1.0 / (12.0 * G.dx2));
     g.i12a2 = split(1.0 / (12.0 * G.dx1 * G.dx1));
     g.i12b2 = split(1.0 / (12.0 * G.dx2 * G.dx2));
+    g.d12a = split(12.0 * G.dx1);
+    g.d12b = split(12.0 * G.dx2);
+    g.c8det = split((144.0 * G.dx1 * G.dx2) * (144.0 * G.dx1 * G.dx2) / 8.0);
     g.grav = split(c->g);
     g.m2a = split(-2.0 * c->atwood);
     g.mu = split(c->mu);

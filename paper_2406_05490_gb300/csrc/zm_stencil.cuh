@@ -62,7 +62,7 @@ __device__ __forceinline__ void geometry_point(const Geom &g, const Tiling &t, i
 {
     const int i = p / g.n2, j = p - (p / g.n2) * g.n2;
     const double *z = y, *w = y + 3 * (size_t)g.N;
-    const double i12a = 1.0 / (12.0 * g.dx1), i12b = 1.0 / (12.0 * g.dx2);
+    const double i12a = g.i12a, i12b = g.i12b;
 
     double a1[3], a2[3], v[5];
 #pragma unroll
@@ -78,18 +78,21 @@ __device__ __forceinline__ void geometry_point(const Geom &g, const Tiling &t, i
     const double det = h11 * h22 - h12 * h12;
     const double w1 = w[p], w2 = w[(size_t)g.N + p];
     const double z3 = z[2 * (size_t)g.N + p];
-    q[p] = grav * z3 + 0.125 * (h22 * w1 * w1 - 2.0 * h12 * w1 * w2 + h11 * w2 * w2) / det;
+    const double quad = h22 * w1 * w1 - 2.0 * h12 * w1 * w2 + h11 * w2 * w2;
 
     if (kKind == kGeoLow) {
+        // unit normal; |a1 x a2|^2 = det (Lagrange's identity) also gives 1/det
         const double nx = a1[1] * a2[2] - a1[2] * a2[1];
         const double ny = a1[2] * a2[0] - a1[0] * a2[2];
         const double nz = a1[0] * a2[1] - a1[1] * a2[0];
-        const double il = 1.0 / sqrt(nx * nx + ny * ny + nz * nz);
+        const double il = dev::rsqrt_nr(nx * nx + ny * ny + nz * nz);
+        q[p] = grav * z3 + 0.125 * quad * (il * il);
         nrm[p] = nx * il;
         nrm[(size_t)g.N + p] = ny * il;
         nrm[2 * (size_t)g.N + p] = nz * il;
         return;
     }
+    q[p] = grav * z3 + 0.125 * quad / det;
     // scaled sheet strength gamma' = (dx1 dx2 / 4 pi) (w1 a2 - w2 a1)
     double gm[3];
 #pragma unroll
@@ -164,11 +167,11 @@ __device__ __forceinline__ void vorticity_point(const Geom &g, int p, const doub
     const size_t N = g.N;
     double v[5];
     line5(phi, i, j, 0, g, 0.0, v);
-    double f1 = -2.0 * atwood * diff1(v, 1.0 / (12.0 * g.dx1));
+    double f1 = -2.0 * atwood * diff1(v, g.i12a);
     line5(phi, i, j, 1, g, 0.0, v);
-    double f2 = -2.0 * atwood * diff1(v, 1.0 / (12.0 * g.dx2));
+    double f2 = -2.0 * atwood * diff1(v, g.i12b);
     if (kVisc) {
-        const double ia = 1.0 / (12.0 * g.dx1 * g.dx1), ib = 1.0 / (12.0 * g.dx2 * g.dx2);
+        const double ia = g.i12a2, ib = g.i12b2;
         const double *w = y + 3 * N;
         line5(w, i, j, 0, g, 0.0, v);
         double l1 = diff2(v, ia);

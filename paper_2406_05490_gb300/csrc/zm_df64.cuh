@@ -216,6 +216,23 @@ __device__ __forceinline__ C2 csub2(C2 x, C2 y)
     return fast_two_sum2(s, add2(e, sub2(x.l, y.l)));
 }
 
+// The same sums without the final renormalisation (8 packed instructions): the result
+// h + l is exact up to the rounding of the low parts, but |l| may exceed half an ulp of h.  Used
+// where the next operation is a sum or product that renormalises (the first layer of a radix-2^2
+// butterfly), so the relaxation does not build up.
+__device__ __forceinline__ C2 cadd2_lazy(C2 x, C2 y)
+{
+    u64 s, e;
+    two_sum2(x.h, y.h, s, e);
+    return C2{s, add2(e, add2(x.l, y.l))};
+}
+__device__ __forceinline__ C2 csub2_lazy(C2 x, C2 y)
+{
+    u64 s, e;
+    two_diff2(x.h, y.h, s, e);
+    return C2{s, add2(e, sub2(x.l, y.l))};
+}
+
 // a * w = a wr + (-a.im, a.re) wi, both products exact in their leading parts (two_prod), summed
 // with one TwoSum and one renormalisation (19 packed instructions): normwise error a few u^2.
 __device__ __forceinline__ C2 cmul2(C2 a, C2 w)

@@ -221,8 +221,8 @@ template <int Q>
 __device__ __forceinline__ void bfly_dif(C2 *v, int m, int e1, int half, const ulonglong2 *__restrict__ tw, int sgn)
 {
     const C2 a0 = v[m], a1 = v[m + Q], a2 = v[m + 2 * Q], a3 = v[m + 3 * Q];
-    const C2 s02 = cadd2(a0, a2), d02 = csub2(a0, a2), s13 = cadd2(a1, a3);
-    const C2 d13 = cmul_i2(csub2(a1, a3), sgn);
+    const C2 s02 = cadd2_lazy(a0, a2), d02 = csub2_lazy(a0, a2), s13 = cadd2_lazy(a1, a3);
+    const C2 d13 = cmul_i2(csub2_lazy(a1, a3), sgn);
     v[m] = cadd2(s02, s13);
     const C2 x2 = csub2(s02, s13), x1 = cadd2(d02, d13), x3 = csub2(d02, d13);
     if (e1 == 0) {
@@ -247,8 +247,8 @@ __device__ __forceinline__ void bfly_dit(C2 *v, int m, int e1, int half, const u
         c2 = cmul2(c2, tw_get(tw, e1, half, sgn));
         c3 = cmul2(c3, tw_get(tw, 3 * e1, half, sgn));
     }
-    const C2 s01 = cadd2(a0, c1), d01 = csub2(a0, c1), s23 = cadd2(c2, c3);
-    const C2 d23 = cmul_i2(csub2(c2, c3), sgn);
+    const C2 s01 = cadd2_lazy(a0, c1), d01 = csub2_lazy(a0, c1), s23 = cadd2_lazy(c2, c3);
+    const C2 d23 = cmul_i2(csub2_lazy(c2, c3), sgn);
     v[m] = cadd2(s01, s23);
     v[m + 2 * Q] = csub2(s01, s23);
     v[m + Q] = cadd2(d01, d23);

@@ -188,3 +188,21 @@ def test_df64_flag_rules(zm):
     with pytest.raises(zm.ZMError) as e:
         zm.zm_create(32, 32, periodic=False, order=zm.ZM_ORDER_LOW | zm.ZM_PREC_DF64)
     assert e.value.code == zm.ZM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("df64", [False, True])
+def test_low_order_4096_full(zm, df64):
+    """The largest FFT side (2^12), 16.8 M points: all of u and dw/dt against the oracle, for the
+    FP64 path (1e-12) and the double-word path (its derived bound)."""
+    n = 4096
+    z, _ = inputs.multi_mode(n, n_modes=8, seed=11, amp=0.02)
+    _, w = inputs.random_state(n, seed=15)
+    m = oracle.Mesh(n, periodic=True)
+    u_ref, wd_ref = oracle.derivative(m, z, w, 0.7, 1.0, 0.0, 0.0, order=oracle.ORDER_LOW)
+    model = zm.ZModel(n, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW, df64=df64)
+    u, wd = model.velocity(z, w)
+    model.close()
+    eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+    tw = wdot_tol(n, 0.0, w, wd_ref) if df64 else TOL
+    print(f"low order 4096^2 df64={df64}: rel L2 u={eu:.3e} wdot={ew:.3e} (bound {tw:.1e})")
+    assert eu <= TOL and ew <= tw

@@ -308,3 +308,58 @@ def test_autotune_keeps_results(zm):
     m64 = zm.ZModel(n, periodic=True, fp32c=False)
     assert zm.zm_autotune(m64.h) == 0  # nothing to tune on the FP64 path
     m64.close()
+
+
+def test_contexts_on_separate_streams_and_threads(zm):
+    """Distinct contexts on distinct streams, driven from distinct host threads at once (state
+    upload, graph-captured steps, state download), give the results each gives alone, bit for
+    bit (every path is deterministic).  Contexts are created and destroyed on the main thread."""
+    import threading
+
+    import torch
+    cases = [dict(n=64, order=zm.ZM_ORDER_HIGH, fp32c=True, df64=False),
+             dict(n=48, order=zm.ZM_ORDER_HIGH, fp32c=False, df64=False),
+             dict(n=128, order=zm.ZM_ORDER_LOW, fp32c=False, df64=True),
+             dict(n=64, order=zm.ZM_ORDER_LOW, fp32c=False, df64=False)]
+
+    def make(case, stream=None):
+        n = case["n"]
+        return zm.ZModel(n, periodic=True, atwood=0.6, g=1.0, delta=0.1 / n, order=case["order"],
+                         fp32c=case["fp32c"], df64=case["df64"],
+                         stream=None if stream is None else stream.cuda_stream)
+
+    def drive(model, case):
+        n = case["n"]
+        z0, _ = inputs.multi_mode(n, n_modes=4, seed=n, amp=0.02)
+        w0 = inputs.random_state(n, seed=n + 1)[1] * 0.1
+        model.set_state(z0, w0)
+        model.step(1e-3, 3)
+        return model.get_state()
+
+    alone = []
+    for c in cases:
+        m = make(c)
+        alone.append(drive(m, c))
+        m.close()
+    streams = [torch.cuda.Stream() for _ in cases]
+    models = [make(c, s) for c, s in zip(cases, streams)]
+    got = [None] * len(cases)
+    errors = []
+
+    def worker(k):
+        try:
+            torch.cuda.set_device(0)
+            got[k] = drive(models[k], cases[k])
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(len(cases))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    for m in models:
+        m.close()
+    assert not errors, errors
+    for a, b in zip(alone, got):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])

@@ -411,7 +411,9 @@ int Batch::derivative(int yin, cudaStream_t s)
     int rc = cuda_check(cudaGetLastError(), "batch geometry launch");
     if (rc) return rc;
     prof_begin(*prof, s, ZM_K_BR, &ev);
-    rc = launch_br32_batch(d, (int)h.size(), nitems, ctas, counter, err, s);
+    bool any_cutoff = false;
+    for (const auto &I : h) any_cutoff = any_cutoff || I.cutoff > 0;
+    rc = launch_br32_batch(d, (int)h.size(), nitems, ctas, counter, err, s, any_cutoff);
     prof_end(*prof, s, ZM_K_BR, ev);
     for (auto &I : h) prof->acc.pairs += (int64_t)I.geom.N * I.geom.N;
     if (rc) return rc;

@@ -75,6 +75,13 @@ __device__ __forceinline__ u64 fadd2(u64 a, u64 b)
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ u64 fsub2(u64 a, u64 b)
+{
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 neg2(u64 a) { return a ^ 0x8000000080000000ull; }
 __device__ __forceinline__ u64 pack2(float lo, float hi)
 {
     u64 d;
@@ -103,6 +110,73 @@ __device__ __forceinline__ int fix_scale(const Inst &I)
     return max(0, min(100, 60 - ilogb(bound)));
 }
 
+// Near pair terms of one source tile (record in shared memory `s`: hi/lo positions and scaled
+// strengths, rows of kTs) for this thread's kR targets (near record row pointer `tr0`): the
+// FP32 hi/lo difference r = (s_hi - t_hi) + (s_lo - t_lo), K = (|r|^2 + delta^2)^(-3/2),
+// r x gamma, with two adjacent sources per packed FP32x2 instruction (even sources in lane 0, odd
+// in lane 1, added at the end).  kMask: keep only pairs with |r|^2 <= c2, |r|^2 formed as
+// fma(rx, rx, fma(ry, ry, rz * rz)) in FP32 (the cutoff decision of the paper's cutoff solver,
+// Sec. 3.2.2, taken on the same FP32 difference by the oracle).
+template <bool kMask>
+__device__ __forceinline__ void near_tile(const float *s, const float *__restrict__ tr0, float d2, float c2,
+                                          float mult, long long (*acc)[kR][kT], int tid)
+{
+    u64 hx[kR], hy[kR], hz[kR], lx[kR], ly[kR], lz[kR], px[kR], py[kR], pz[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const float *tr = tr0 + r * kT;
+        float v;
+        v = __ldg(tr);
+        hx[r] = pack2(v, v);
+        v = __ldg(tr + kTs);
+        hy[r] = pack2(v, v);
+        v = __ldg(tr + 2 * kTs);
+        hz[r] = pack2(v, v);
+        v = __ldg(tr + 3 * kTs);
+        lx[r] = pack2(v, v);
+        v = __ldg(tr + 4 * kTs);
+        ly[r] = pack2(v, v);
+        v = __ldg(tr + 5 * kTs);
+        lz[r] = pack2(v, v);
+        px[r] = py[r] = pz[r] = 0ull;
+    }
+    const u64 d22 = pack2(d2, d2);
+    const u64 *s2 = reinterpret_cast<const u64 *>(s);  // row k at s2[k * kTs / 2]
+    constexpr int H = kTs / 2;
+#pragma unroll 2
+    for (int m = 0; m < H; ++m) {
+        const u64 shx = s2[m], shy = s2[H + m], shz = s2[2 * H + m];
+        const u64 slx = s2[3 * H + m], sly = s2[4 * H + m], slz = s2[5 * H + m];
+        const u64 gx = s2[6 * H + m], gy = s2[7 * H + m], gz = s2[8 * H + m];
+        const u64 ngx = neg2(gx), ngy = neg2(gy), ngz = neg2(gz);
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const u64 rx = fadd2(fsub2(shx, hx[r]), fsub2(slx, lx[r]));
+            const u64 ry = fadd2(fsub2(shy, hy[r]), fsub2(sly, ly[r]));
+            const u64 rz = fadd2(fsub2(shz, hz[r]), fsub2(slz, lz[r]));
+            const u64 q = ffma2(rx, rx, ffma2(ry, ry, ffma2(rz, rz, d22)));
+            const u64 iq = rsqrt2(q);
+            u64 kk = fmul2(fmul2(iq, iq), iq);
+            if (kMask) {
+                const u64 r2 = ffma2(rx, rx, ffma2(ry, ry, fmul2(rz, rz)));
+                float r2a, r2b, ka, kb;
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(r2a), "=f"(r2b) : "l"(r2));
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(ka), "=f"(kb) : "l"(kk));
+                kk = pack2(r2a <= c2 ? ka : 0.0f, r2b <= c2 ? kb : 0.0f);
+            }
+            px[r] = ffma2(kk, ffma2(ry, gz, fmul2(rz, ngy)), px[r]);
+            py[r] = ffma2(kk, ffma2(rz, gx, fmul2(rx, ngz)), py[r]);
+            pz[r] = ffma2(kk, ffma2(rx, gy, fmul2(ry, ngx)), pz[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        acc[0][r][tid] += __float2ll_rn(sum2(px[r]) * mult);
+        acc[1][r][tid] += __float2ll_rn(sum2(py[r]) * mult);
+        acc[2][r][tid] += __float2ll_rn(sum2(pz[r]) * mult);
+    }
+}
+
 struct Unit {
     int inst;  // -1: no more work
     int tile;  // target tile
@@ -110,6 +184,9 @@ struct Unit {
     int far;
 };
 
+// kCut: some interface of the batch sums within a cutoff, so straddling tile pairs (masked
+// near path) can occur; without it that path is compiled out.
+template <bool kCut>
 __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
     br32_batch_kernel(const Inst *__restrict__ insts, int ninst, long long nitems,
                       unsigned long long *counter, int *err)
@@ -287,46 +364,11 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
                     acc[1][r][tid] += __float2ll_rn(vy * c_mult);
                     acc[2][r][tid] += __float2ll_rn(vz * c_mult);
                 }
+            } else if (!kCut || un.far == 0) {
+                near_tile<false>(s, c_near + (size_t)c_tile * kRec32 * kTs + tid, c_d2, 0.0f, c_mult, acc, tid);
             } else {
-                // ---- near path (masked at the cutoff when the tile straddles it) ---------
-                const float c2 = (un.far == 2) ? c_c2 : __int_as_float(0x7f800000);
-                float hx[kR], hy[kR], hz[kR], lx[kR], ly[kR], lz[kR], px[kR], py[kR], pz[kR];
-#pragma unroll
-                for (int r = 0; r < kR; ++r) {
-                    const float *tr = c_near + (size_t)c_tile * kRec32 * kTs + r * kT + tid;
-                    hx[r] = __ldg(tr);
-                    hy[r] = __ldg(tr + kTs);
-                    hz[r] = __ldg(tr + 2 * kTs);
-                    lx[r] = __ldg(tr + 3 * kTs);
-                    ly[r] = __ldg(tr + 4 * kTs);
-                    lz[r] = __ldg(tr + 5 * kTs);
-                    px[r] = py[r] = pz[r] = 0.0f;
-                }
-#pragma unroll 2
-                for (int j = 0; j < kTs; ++j) {
-                    const float shx = s[j], shy = s[kTs + j], shz = s[2 * kTs + j];
-                    const float slx = s[3 * kTs + j], sly = s[4 * kTs + j], slz = s[5 * kTs + j];
-                    const float gx = s[6 * kTs + j], gy = s[7 * kTs + j], gz = s[8 * kTs + j];
-#pragma unroll
-                    for (int r = 0; r < kR; ++r) {
-                        const float rx = (shx - hx[r]) + (slx - lx[r]);
-                        const float ry = (shy - hy[r]) + (sly - ly[r]);
-                        const float rz = (shz - hz[r]) + (slz - lz[r]);
-                        const float q = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, c_d2)));
-                        const float iq = dev::rsqrt_approx(q);
-                        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                        const float kk = (r2 <= c2) ? iq * iq * iq : 0.0f;
-                        px[r] = fmaf(kk, fmaf(ry, gz, -rz * gy), px[r]);
-                        py[r] = fmaf(kk, fmaf(rz, gx, -rx * gz), py[r]);
-                        pz[r] = fmaf(kk, fmaf(rx, gy, -ry * gx), pz[r]);
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < kR; ++r) {
-                    acc[0][r][tid] += __float2ll_rn(px[r] * c_mult);
-                    acc[1][r][tid] += __float2ll_rn(py[r] * c_mult);
-                    acc[2][r][tid] += __float2ll_rn(pz[r] * c_mult);
-                }
+                // the tile pair straddles the cutoff: mask each pair by its FP32 distance
+                near_tile<true>(s, c_near + (size_t)c_tile * kRec32 * kTs + tid, c_d2, c_c2, c_mult, acc, tid);
             }
         }
         bad = __syncthreads_or(!ok);
@@ -368,12 +410,14 @@ __global__ void init_far_kernel(float *far_rec, size_t ntiles, float d2)
 int br32_occupancy()
 {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, br32_batch_kernel, kT, 0) != cudaSuccess ||
-        occ < 1) {
+    int occ_cut = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, br32_batch_kernel<false>, kT, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cut, br32_batch_kernel<true>, kT, 0) != cudaSuccess ||
+        occ < 1 || occ_cut < 1) {
         cudaGetLastError();
-        occ = 1;
+        return 1;
     }
-    return occ;
+    return std::min(occ, occ_cut);
 }
 
 void init_far_records(float *far_rec, int ntiles, float d2, cudaStream_t s)
@@ -382,9 +426,12 @@ void init_far_records(float *far_rec, int ntiles, float d2, cudaStream_t s)
 }
 
 int launch_br32_batch(const Inst *d_insts, int ninst, long long nitems, int ctas,
-                      unsigned long long *counter, int *err, cudaStream_t s)
+                      unsigned long long *counter, int *err, cudaStream_t s, bool any_cutoff)
 {
-    br32_batch_kernel<<<ctas, kT, 0, s>>>(d_insts, ninst, nitems, counter, err);
+    if (any_cutoff)
+        br32_batch_kernel<true><<<ctas, kT, 0, s>>>(d_insts, ninst, nitems, counter, err);
+    else
+        br32_batch_kernel<false><<<ctas, kT, 0, s>>>(d_insts, ninst, nitems, counter, err);
     return cuda_check(cudaGetLastError(), "Birkhoff-Rott FP32C kernel launch");
 }
 

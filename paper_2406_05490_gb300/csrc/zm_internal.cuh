@@ -184,7 +184,7 @@ int launch_br(zm_ctx *c, const double *y);  // FP64 path (then launch_reduce)
 // ---- FP32C Birkhoff-Rott kernel over a batch of interfaces (zm_br32.cu) ----------------------------
 int br32_occupancy();  // resident CTAs per SM of the batched kernel
 int launch_br32_batch(const Inst *d_insts, int ninst, long long nitems, int ctas,
-                      unsigned long long *counter, int *err, cudaStream_t s);
+                      unsigned long long *counter, int *err, cudaStream_t s, bool any_cutoff);
 void init_far_records(float *far_rec, int ntiles, float d2, cudaStream_t s);
 
 // ---- low order (zm_fft.cu) ---------------------------------------------------------------------

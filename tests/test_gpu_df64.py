@@ -8,7 +8,7 @@ roundoff of a double word:
     Phi and w are stored and formed with ~4 u^2 relative rounding per node, independently from
     node to node; the 4th-order first difference amplifies such noise by its coefficient norm
     0.95 / dx = 0.95 n (relative to |D Phi| >= 2 pi |Phi| for the lowest mode), the Laplacian
-    (two axes) by 4.4 / dx^2.  So at 4096^2 the bound is ~1.5e-11 where the FP64 path stays
+    (two axes) by 4.4 / dx^2.  So at 4096^2 the bound is ~9e-12 where the FP64 path stays
     at 1e-12: 48 bits are 5 fewer than FP64's 53.
   stepped state: 1e-12 on z and w, 1e-10 on the displacement z - z0 (as for the FP64 path).
 z1 and z2 are stored relative to the mesh coordinates, so the amplification acts on the

@@ -61,3 +61,17 @@ def test_binding_resolves_every_entry_point():
         if name.startswith("zm_") and inspect.isfunction(getattr(zm, name)):
             assert name in declared, name
             assert hasattr(lib, name)
+
+
+def test_binding_constants_match_header():
+    """Every integer #define of include/zm.h (status codes, order and precision flags, kernel
+    classes, request states) has the same value in the Python binding."""
+    from paper_2406_05490_gb300 import zm
+    src = open(os.path.join(ROOT, "include", "zm.h")).read()
+    found = 0
+    for m in re.finditer(r"^#define\s+(ZM_\w+)\s+\(?(-?(?:0x[0-9a-fA-F]+|\d+))\)?", src, flags=re.M):
+        name, value = m.group(1), int(m.group(2), 0)
+        assert hasattr(zm, name), name
+        assert getattr(zm, name) == value, (name, getattr(zm, name), value)
+        found += 1
+    assert found >= 24

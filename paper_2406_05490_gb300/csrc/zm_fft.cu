@@ -50,7 +50,8 @@ __device__ void fft_dif(double2 *x, int rows, int L, const double2 *__restrict__
             double2 *xr = x + (size_t)row * L;
             const double2 u = xr[a], v = xr[a + h];
             xr[a] = make_double2(u.x + v.x, u.y + v.y);
-            xr[a + h] = cmul(make_double2(u.x - v.x, u.y - v.y), twiddle(tw, pos * tstride, sgn));
+            const double2 d = make_double2(u.x - v.x, u.y - v.y);
+            xr[a + h] = pos ? cmul(d, twiddle(tw, pos * tstride, sgn)) : d;  // W^0 = 1
         }
         __syncthreads();
     }
@@ -66,7 +67,7 @@ __device__ void fft_dit(double2 *x, int rows, int L, const double2 *__restrict__
             const int row = b / half, idx = b - row * half;
             const int pos = idx & (h - 1), a = ((idx - pos) << 1) + pos;
             double2 *xr = x + (size_t)row * L;
-            const double2 u = xr[a], v = cmul(xr[a + h], twiddle(tw, pos * tstride, sgn));
+            const double2 u = xr[a], v = pos ? cmul(xr[a + h], twiddle(tw, pos * tstride, sgn)) : xr[a + h];
             xr[a] = make_double2(u.x + v.x, u.y + v.y);
             xr[a + h] = make_double2(u.x - v.x, u.y - v.y);
         }

@@ -197,6 +197,9 @@ __global__ void __launch_bounds__(kTpb)
 #ifndef ZM_DF_KMAX
 #define ZM_DF_KMAX 4  // most radix-2 stages per register group (group of 2^K values)
 #endif
+#ifndef ZM_DF_REGS
+#define ZM_DF_REGS 128  // register budget per thread the FFT passes are compiled for
+#endif
 #ifndef ZM_DF_ELEMS
 #define ZM_DF_ELEMS 4096  // complex values per CTA of an FFT pass (rows * row length)
 #endif
@@ -394,11 +397,11 @@ __device__ __forceinline__ ulonglong2 c2_pack(float2 re, float2 im)
 }
 
 // Threads per CTA and resident CTAs per SM of the passes over rows of length 2^L: one group of
-// 16 values per thread over the CTA's kFftElems values (a single row when it is longer), with the
-// register budget of 128 per thread that this occupancy leaves.
+// 16 values per thread over the CTA's kFftElems values (a single row when it is longer), as many
+// CTAs per SM as a budget of ZM_DF_REGS registers per thread allows.
 constexpr int elems_for(int L) { return (1 << L) > kFftElems ? (1 << L) : kFftElems; }
 constexpr int threads_for(int L) { return elems_for(L) / 16; }
-constexpr int minb_for(int L) { return 65536 / (threads_for(L) * 128); }
+constexpr int minb_for(int L) { return 65536 / (threads_for(L) * ZM_DF_REGS); }
 
 // pass A: rows i (length n2 = 2^L) of c = w1 + i w2; forward; write out[j][i] (transposed).
 template <int L>

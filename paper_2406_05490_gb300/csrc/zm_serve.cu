@@ -108,6 +108,7 @@ public:
     {
         cudaSetDevice(device);
         std::vector<Request *> admitted, finished;
+        int stable = 0;  // iterations since the resident set last changed
         while (true) {
             admitted.clear();
             {
@@ -170,17 +171,22 @@ public:
             if (changed || batch.h.size() != running.size()) {
                 batch.h.clear();
                 for (Request *r : running) batch.h.push_back(r->inst);
-                int rc = batch.plan();
+                int rc = batch.plan();  // drops the captured step graph
                 if (rc) {
                     fail_all(rc);
                     continue;
                 }
+                stable = 0;
+            } else {
+                ++stable;
             }
             peak_slots = std::max(peak_slots, (int)running.size());
             bool any_work = false;
             for (Request *r : running) any_work |= r->remaining > 0;
             if (any_work) {
-                int rc = batch.step(1, false);
+                // plain launches right after a membership change; once the same set has run an
+                // iteration, the step is captured as a graph and replayed until the set changes
+                int rc = batch.step(1, stable >= 1);
                 if (rc) {
                     fail_all(rc);
                     continue;

@@ -155,7 +155,8 @@ BrPlan plan_br(const Geom &g, const Tiling &t, int sm_count)
         p.tpb = kTpb64s;
         p.ntb = (g.N + p.tpb * p.r - 1) / (p.tpb * p.r);
         p.qsplit = 1;
-        while (p.qsplit < 4 && (long long)p.ntb * t.ntiles * p.qsplit < want) p.qsplit *= 2;
+        // up to 16 slices of 16 sources: a 32^2 mesh then runs 1024 one-warp CTAs (~7 per SM)
+        while (p.qsplit < 16 && (long long)p.ntb * t.ntiles * p.qsplit < want) p.qsplit *= 2;
         if (p.qsplit > 1) {
             p.tiles_per_split = 1;
             p.nsplit = t.ntiles * p.qsplit;

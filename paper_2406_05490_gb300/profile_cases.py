@@ -6,6 +6,7 @@ configuration through the C ABI, nothing else.
     python -m paper_2406_05490_gb300.profile_cases high32 256 2     # FP32C high order
     python -m paper_2406_05490_gb300.profile_cases high64 128 2     # FP64 high order
     python -m paper_2406_05490_gb300.profile_cases batch 64 2       # 64 ragged interfaces
+    python -m paper_2406_05490_gb300.profile_cases single 32 10     # single mode, free edges, FP64
 """
 from __future__ import annotations
 
@@ -30,6 +31,14 @@ def main(argv):
         zm.zm_batch_step(h, 1e-3, steps)
         zm.zm_batch_sync(h)
         zm.zm_batch_destroy(h)
+        return 0
+    if kind == "single":
+        z, w = inputs.single_mode(size)
+        model = zm.ZModel(size, periodic=False, atwood=0.5, g=1.0, delta=0.1 / size)
+        model.set_state(z, w)
+        model.step(1e-3, steps)
+        model.sync()
+        model.close()
         return 0
     order = zm.ZM_ORDER_LOW if kind in ("low", "lowdf") else zm.ZM_ORDER_HIGH
     z, _ = inputs.multi_mode(size, n_modes=8, seed=7, amp=0.02)

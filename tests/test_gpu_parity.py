@@ -363,3 +363,39 @@ def test_contexts_on_separate_streams_and_threads(zm):
     assert not errors, errors
     for a, b in zip(alone, got):
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("order,fp32c,df64,n", [("high", False, False, 48), ("high", True, False, 64),
+                                                ("low", False, False, 64), ("low", False, True, 64),
+                                                ("medium", True, False, 32)])
+def test_checkpoint_resume(zm, order, fp32c, df64, n):
+    """Six steps in one go equal three steps, a checkpoint (zm_get_state), a fresh context
+    restored from it (zm_set_state) and three more steps: bit for bit where the resident state is
+    FP64 (FP64 and FP32C contexts); within two units of the double word's rounding where it is
+    held as FP32 pairs (the checkpoint passes through FP64)."""
+    od = {"high": zm.ZM_ORDER_HIGH, "low": zm.ZM_ORDER_LOW, "medium": zm.ZM_ORDER_MEDIUM}[order]
+    z0, _ = inputs.multi_mode(n, n_modes=4, seed=n + 5, amp=0.02)
+    w0 = inputs.random_state(n, seed=n + 6)[1] * 0.1
+
+    def make():
+        return zm.ZModel(n, periodic=True, atwood=0.6, g=1.0, delta=0.1 / n, order=od, fp32c=fp32c, df64=df64)
+
+    a = make()
+    a.set_state(z0, w0)
+    a.step(1e-3, 6)
+    z6, w6 = a.get_state()
+    a.close()
+    b = make()
+    b.set_state(z0, w0)
+    b.step(1e-3, 3)
+    zc, wc = b.get_state()
+    b.close()
+    c = make()
+    c.set_state(zc, wc)
+    c.step(1e-3, 3)
+    z6r, w6r = c.get_state()
+    c.close()
+    if df64:
+        assert rel(z6r, z6) <= 1e-15 and rel(w6r, w6) <= 1e-13
+    else:
+        assert np.array_equal(z6r, z6) and np.array_equal(w6r, w6)

@@ -113,6 +113,48 @@ __device__ __forceinline__ df rsqrt(df x)
     return fast_two_sum(s.hi, __fadd_rn(s.lo, __fmul_rn(0.5f, __fadd_rn(c.lo, rest))));
 }
 
+// Fused forms for the stencil pass, each one renormalisation instead of several: the rounding
+// errors of the leading-part operations are captured exactly (TwoSum / FMA product error) and
+// added, with the low parts, in FP32, as in the sloppy sum (normwise error a few u^2).
+//   stencil_s:  (m2 - p2) + 8 (p1 - m1)                 28 flops (35 as separate sums)
+//   mul_sub:    a b - c d                               19 flops (27)
+//   sum_sq3:    x^2 + y^2 + z^2                         31 flops (43), no cancellation
+__device__ __forceinline__ df stencil_s(df m2, df m1, df p1, df p2)
+{
+    const df a = two_sum(m2.hi, -p2.hi);
+    const df b = two_sum(p1.hi, -m1.hi);
+    const df s = two_sum(a.hi, __fmul_rn(8.0f, b.hi));  // 8 b.hi is exact
+    float t = __fadd_rn(__fsub_rn(m2.lo, p2.lo), __fmul_rn(8.0f, __fsub_rn(p1.lo, m1.lo)));
+    t = __fadd_rn(t, __fadd_rn(a.lo, __fmaf_rn(8.0f, b.lo, s.lo)));
+    return fast_two_sum(s.hi, t);
+}
+
+__device__ __forceinline__ df mul_sub(df a, df b, df c, df d)
+{
+    const df p = two_prod(a.hi, b.hi);
+    const df q = two_prod(c.hi, d.hi);
+    const df s = two_sum(p.hi, -q.hi);
+    float t = __fadd_rn(s.lo, __fsub_rn(p.lo, q.lo));
+    t = __fmaf_rn(a.hi, b.lo, t);
+    t = __fmaf_rn(a.lo, b.hi, t);
+    t = __fmaf_rn(-c.hi, d.lo, t);
+    t = __fmaf_rn(-c.lo, d.hi, t);
+    return fast_two_sum(s.hi, t);
+}
+
+__device__ __forceinline__ df sum_sq3(df x, df y, df z)
+{
+    const df a = two_prod(x.hi, x.hi), b = two_prod(y.hi, y.hi), c = two_prod(z.hi, z.hi);
+    const df s1 = two_sum(a.hi, b.hi);
+    const df s2 = two_sum(s1.hi, c.hi);
+    float t = __fadd_rn(__fadd_rn(a.lo, b.lo), c.lo);
+    t = __fadd_rn(t, __fadd_rn(s1.lo, s2.lo));
+    t = __fmaf_rn(__fadd_rn(x.hi, x.hi), x.lo, t);
+    t = __fmaf_rn(__fadd_rn(y.hi, y.hi), y.lo, t);
+    t = __fmaf_rn(__fadd_rn(z.hi, z.hi), z.lo, t);
+    return fast_two_sum(s2.hi, t);
+}
+
 // Complex double-word number, stored as float4 {re.hi, re.lo, im.hi, im.lo}.
 struct cdf {
     df re, im;

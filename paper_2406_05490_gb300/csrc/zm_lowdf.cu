@@ -75,9 +75,7 @@ __device__ __forceinline__ Nb nb_axis1(int i, int j, const DfGeo &g)
 // (f-2 - f+2) + 8 (f+1 - f-1): 12 dx times the 4th-order first difference
 __device__ __forceinline__ df diff1_s(const float2 *__restrict__ f, const Nb &n)
 {
-    const df a = sub(ldf(f, n.m2), ldf(f, n.p2));
-    const df b = sub(ldf(f, n.p1), ldf(f, n.m1));
-    return add(a, scale2(b, 8.0f));
+    return stencil_s(ldf(f, n.m2), ldf(f, n.m1), ldf(f, n.p1), ldf(f, n.p2));
 }
 
 // ((f-2 - f+2) + 8 (f+1 - f-1)) / (12 dx)
@@ -117,20 +115,20 @@ __global__ void __launch_bounds__(kTpb)
     }
     b1[0] = add(dc(g.d12a), b1[0]);  // the mesh coordinate's share: 12 dx1 along alpha1
     b2[1] = add(dc(g.d12b), b2[1]);
-    const df nx = sub(mul(b1[1], b2[2]), mul(b1[2], b2[1]));
-    const df ny = sub(mul(b1[2], b2[0]), mul(b1[0], b2[2]));
-    const df nz = sub(mul(b1[0], b2[1]), mul(b1[1], b2[0]));
-    const df rs = rsqrt(add(add(sqr(nx), sqr(ny)), sqr(nz)));
+    const df nx = mul_sub(b1[1], b2[2], b1[2], b2[1]);
+    const df ny = mul_sub(b1[2], b2[0], b1[0], b2[2]);
+    const df nz = mul_sub(b1[0], b2[1], b1[1], b2[0]);
+    const df rs = rsqrt(sum_sq3(nx, ny, nz));
     nrm[p] = to_f2(mul(nx, rs));
     nrm[N + p] = to_f2(mul(ny, rs));
     nrm[2 * N + p] = to_f2(mul(nz, rs));
 
     // gamma = (w1 / (12 dx2)) b2 - (w2 / (12 dx1)) b1
     const df s1 = mul(ldf(y, 3 * N + p), dc(g.i12b)), s2 = mul(ldf(y, 4 * N + p), dc(g.i12a));
-    const df gx = sub(mul(s1, b2[0]), mul(s2, b1[0]));
-    const df gy = sub(mul(s1, b2[1]), mul(s2, b1[1]));
-    const df gz = sub(mul(s1, b2[2]), mul(s2, b1[2]));
-    const df g2 = add(add(sqr(gx), sqr(gy)), sqr(gz));
+    const df gx = mul_sub(s1, b2[0], s2, b1[0]);
+    const df gy = mul_sub(s1, b2[1], s2, b1[1]);
+    const df gz = mul_sub(s1, b2[2], s2, b1[2]);
+    const df g2 = sum_sq3(gx, gy, gz);
     // 1/8 |gamma|^2 / det = 1/8 |gamma|^2 rs^2 (144 dx1 dx2)^2
     const df jump = mul(mul(g2, sqr(rs)), dc(g.c8det));
     q[p] = to_f2(add(mul(dc(g.grav), ldf(y, 2 * N + p)), jump));

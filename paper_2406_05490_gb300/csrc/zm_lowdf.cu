@@ -38,7 +38,8 @@ inline Dc split(double v)
 }
 
 __device__ __forceinline__ df dc(Dc c) { return df{c.hi, c.lo}; }
-__device__ __forceinline__ df ldf(const float2 *__restrict__ f, size_t k) { return from_f2(f[k]); }
+// Node offsets are 32-bit: low order is limited to 4096^2 = 2^24 nodes, so 5N < 2^31.
+__device__ __forceinline__ df ldf(const float2 *__restrict__ f, int k) { return from_f2(f[k]); }
 
 struct DfGeo {
     int n1, n2, l2;
@@ -55,20 +56,20 @@ struct DfGeo {
 // Periodic 4th-order first difference along one axis at node p: the four neighbours are
 // p + k * stride for k = -2, -1, 1, 2 after wrapping the axis index c0 + k into [0, n).
 struct Nb {
-    size_t m2, m1, p1, p2;
+    int m2, m1, p1, p2;
 };
 
 __device__ __forceinline__ Nb nb_axis0(int i, int j, const DfGeo &g)
 {
     const int m = g.n1 - 1;
-    return Nb{((size_t)((i - 2) & m) << g.l2) + j, ((size_t)((i - 1) & m) << g.l2) + j,
-              ((size_t)((i + 1) & m) << g.l2) + j, ((size_t)((i + 2) & m) << g.l2) + j};
+    return Nb{(((i - 2) & m) << g.l2) + j, (((i - 1) & m) << g.l2) + j, (((i + 1) & m) << g.l2) + j,
+              (((i + 2) & m) << g.l2) + j};
 }
 
 __device__ __forceinline__ Nb nb_axis1(int i, int j, const DfGeo &g)
 {
     const int m = g.n2 - 1;
-    const size_t r = (size_t)i << g.l2;
+    const int r = i << g.l2;
     return Nb{r + ((j - 2) & m), r + ((j - 1) & m), r + ((j + 1) & m), r + ((j + 2) & m)};
 }
 
@@ -86,7 +87,7 @@ __device__ __forceinline__ df diff1_df(const float2 *__restrict__ f, const Nb &n
 
 // (16 (f-1 + f+1) - (f-2 + f+2) - 30 f0) / (12 dx^2), accurate sums: the three groups cancel
 // to O(dx^2) of their size.
-__device__ __forceinline__ df diff2_df(const float2 *__restrict__ f, const Nb &n, size_t p0, df inv12sq)
+__device__ __forceinline__ df diff2_df(const float2 *__restrict__ f, const Nb &n, int p0, df inv12sq)
 {
     const df s1 = add_acc(ldf(f, n.m1), ldf(f, n.p1));
     const df s2 = add_acc(ldf(f, n.m2), ldf(f, n.p2));
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(kTpb)
     const int p = blockIdx.x * kTpb + threadIdx.x;
     if (p >= g.N) return;
     const int i = p >> g.l2, j = p & (g.n2 - 1);
-    const size_t N = g.N;
+    const int N = g.N;
     const Nb na = nb_axis0(i, j, g), nb = nb_axis1(i, j, g);
     df b1[3], b2[3];
 #pragma unroll
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kTpb)
     const int p = blockIdx.x * kTpb + threadIdx.x;
     if (p >= g.N) return;
     const int i = p >> g.l2, j = p & (g.n2 - 1);
-    const size_t N = g.N;
+    const int N = g.N;
     const Nb na = nb_axis0(i, j, g), nb = nb_axis1(i, j, g);
     const df m2a = dc(g.m2a);
     df f1 = mul(m2a, diff1_df(phi, na, dc(g.i12a)));

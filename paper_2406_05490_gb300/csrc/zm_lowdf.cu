@@ -179,8 +179,8 @@ __global__ void __launch_bounds__(kTpb)
 // forward, Riesz multiplier, inverse, transposed write; rows inverse with the velocity
 // epilogue), on complex double words in packed FP32x2 instructions.
 //
-// Each pass holds `rows` complete rows (rows * L = 4096 complex values, 68 KiB with padding)
-// in shared memory.  The log2 L radix-2 stages are done in chunks of K <= 4 stages: a thread
+// Each pass holds `rows` complete rows (rows * L up to 4096 complex values, 68 KiB with padding;
+// a single row of 4096 at the largest side) in shared memory.  The log2 L radix-2 stages are done in chunks of K <= 4 stages: a thread
 // loads a group of 2^K values spaced h apart into registers, applies the chunk's stages there
 // and writes the group back, so shared memory is traversed once per chunk rather than once per
 // stage.  Inside a chunk, pairs of stages are fused as radix-2^2 butterflies (three twiddle
@@ -626,7 +626,6 @@ DfGeo make_geo(const zm_ctx *c)
 
 inline const float2 *F2(const double *p) { return reinterpret_cast<const float2 *>(p); }
 inline float2 *F2(double *p) { return reinterpret_cast<float2 *>(p); }
-inline const ulonglong2 *U2(const double2 *p) { return reinterpret_cast<const ulonglong2 *>(p); }
 inline ulonglong2 *U2(double2 *p) { return reinterpret_cast<ulonglong2 *>(p); }
 
 // Launches of the three passes for rows of length 2^L.  Each sets the kernel's dynamic shared

@@ -11,7 +11,7 @@
 //   pass B: rows of the transpose (along alpha1) forward, multiply by -(k2 + i k1)/|k|,
 //           inverse along alpha1, transposed write                  [n2][n1] -> [n1][n2]
 //   pass C: rows inverse along alpha2, real part / (n1 n2), epilogue u = -s/2 N, Phi.
-// Each CTA holds `rows` complete rows in shared memory and runs radix-2 butterflies there:
+// Each CTA holds `rows` complete rows in shared memory and runs radix-2^2 butterflies there:
 // decimation in frequency (natural order in, bit-reversed out) for the forward transforms and
 // for pass C, decimation in time (bit-reversed in, natural out) for the inverse of pass B.
 #include <algorithm>
@@ -30,46 +30,107 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 
 __device__ __forceinline__ int bitrev(int j, int logL) { return (int)(__brev((unsigned)j) >> (32 - logL)); }
 
-// tw[k] = exp(-2 pi i k / L), k < L/2.  sgn = +1 uses conj (inverse transform).
-__device__ __forceinline__ double2 twiddle(const double2 *__restrict__ tw, int k, int sgn)
+// W_L^k = exp(-2 pi i k / L) for 0 <= k < 3L/4 from the half table tw[k] (k < L/2), using
+// W_L^(k + L/2) = -W_L^k; conjugated for the inverse (sgn = +1).
+__device__ __forceinline__ double2 twiddle(const double2 *__restrict__ tw, int k, int half, int sgn)
 {
-    double2 w = tw[k];
+    double2 w = tw[k >= half ? k - half : k];
+    if (k >= half) w = make_double2(-w.x, -w.y);
     if (sgn > 0) w.y = -w.y;
     return w;
 }
 
-// Decimation in frequency, in place on `rows` rows of length L in shared memory.
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+// a * (+i) for s > 0, a * (-i) for s < 0 (exact)
+__device__ __forceinline__ double2 cmul_pm_i(double2 a, int s)
+{
+    return s > 0 ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
+}
+
+// Decimation in frequency, in place on `rows` rows of length L = 2^l >= 8 in shared memory:
+// natural order in, bit-reversed order out.  Pairs of radix-2 stages (spans 2h, h) are fused
+// into radix-2^2 butterflies on x[p], x[p+h], x[p+2h], x[p+3h] of a block of 4h, which take three
+// twiddle products per four values instead of four and keep the radix-2 output order; when
+// log2 L is odd, one radix-2 stage (span L/2) comes first.  W^0 = 1 products are skipped.
 __device__ void fft_dif(double2 *x, int rows, int L, const double2 *__restrict__ tw, int sgn)
 {
-    const int half = L >> 1;
-    for (int h = half; h >= 1; h >>= 1) {
-        const int tstride = half / h;  // twiddle index step for this stage
+    const int l = __ffs(L) - 1, half = L >> 1, quarter = L >> 2;
+    if (l & 1) {
         for (int b = threadIdx.x; b < rows * half; b += blockDim.x) {
-            const int row = b / half, idx = b - row * half;
-            const int pos = idx & (h - 1), a = ((idx - pos) << 1) + pos;
-            double2 *xr = x + (size_t)row * L;
-            const double2 u = xr[a], v = xr[a + h];
-            xr[a] = make_double2(u.x + v.x, u.y + v.y);
-            const double2 d = make_double2(u.x - v.x, u.y - v.y);
-            xr[a + h] = pos ? cmul(d, twiddle(tw, pos * tstride, sgn)) : d;  // W^0 = 1
+            const int row = b >> (l - 1), pos = b & (half - 1);
+            double2 *xr = x + ((size_t)row << l);
+            const double2 u = xr[pos], v = xr[pos + half];
+            xr[pos] = cadd(u, v);
+            const double2 d = csub(u, v);
+            xr[pos + half] = pos ? cmul(d, twiddle(tw, pos, half, sgn)) : d;
+        }
+        __syncthreads();
+    }
+    for (int h = (l & 1) ? (L >> 3) : (L >> 2); h >= 1; h >>= 2) {
+        const int lh = __ffs(h) - 1;
+        const int step = half / (2 * h);  // W_{4h}^m = W_L^(m * step)
+        for (int b = threadIdx.x; b < rows * quarter; b += blockDim.x) {
+            const int row = b >> (l - 2), idx = b & (quarter - 1);
+            const int pos = idx & (h - 1);
+            double2 *xr = x + ((size_t)row << l) + ((idx >> lh) << (lh + 2)) + pos;
+            const double2 a0 = xr[0], a1 = xr[h], a2 = xr[2 * h], a3 = xr[3 * h];
+            const double2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3);
+            const double2 d13 = cmul_pm_i(csub(a1, a3), sgn);  // times W_{4h}^h = -+i
+            const double2 x2 = csub(s02, s13), x1 = cadd(d02, d13), x3 = csub(d02, d13);
+            xr[0] = cadd(s02, s13);
+            const int e1 = pos * step;
+            if (e1 == 0) {
+                xr[h] = x2;
+                xr[2 * h] = x1;
+                xr[3 * h] = x3;
+            } else {
+                xr[h] = cmul(x2, twiddle(tw, 2 * e1, half, sgn));
+                xr[2 * h] = cmul(x1, twiddle(tw, e1, half, sgn));
+                xr[3 * h] = cmul(x3, twiddle(tw, 3 * e1, half, sgn));
+            }
         }
         __syncthreads();
     }
 }
 
-// Decimation in time, in place (bit-reversed input, natural output).
+// Decimation in time, in place: bit-reversed order in, natural order out (the mirror of fft_dif:
+// fused pairs of spans (h, 2h) from h = 1, then one radix-2 stage of span L/2 when log2 L is odd).
 __device__ void fft_dit(double2 *x, int rows, int L, const double2 *__restrict__ tw, int sgn)
 {
-    const int half = L >> 1;
-    for (int h = 1; h <= half; h <<= 1) {
-        const int tstride = half / h;
+    const int l = __ffs(L) - 1, half = L >> 1, quarter = L >> 2;
+    for (int h = 1; 4 * h <= L; h <<= 2) {
+        const int lh = __ffs(h) - 1;
+        const int step = half / (2 * h);
+        for (int b = threadIdx.x; b < rows * quarter; b += blockDim.x) {
+            const int row = b >> (l - 2), idx = b & (quarter - 1);
+            const int pos = idx & (h - 1);
+            double2 *xr = x + ((size_t)row << l) + ((idx >> lh) << (lh + 2)) + pos;
+            const double2 a0 = xr[0];
+            double2 c1 = xr[h], c2 = xr[2 * h], c3 = xr[3 * h];
+            const int e1 = pos * step;
+            if (e1) {
+                c1 = cmul(c1, twiddle(tw, 2 * e1, half, sgn));
+                c2 = cmul(c2, twiddle(tw, e1, half, sgn));
+                c3 = cmul(c3, twiddle(tw, 3 * e1, half, sgn));
+            }
+            const double2 s01 = cadd(a0, c1), d01 = csub(a0, c1), s23 = cadd(c2, c3);
+            const double2 d23 = cmul_pm_i(csub(c2, c3), sgn);
+            xr[0] = cadd(s01, s23);
+            xr[2 * h] = csub(s01, s23);
+            xr[h] = cadd(d01, d23);
+            xr[3 * h] = csub(d01, d23);
+        }
+        __syncthreads();
+    }
+    if (l & 1) {
         for (int b = threadIdx.x; b < rows * half; b += blockDim.x) {
-            const int row = b / half, idx = b - row * half;
-            const int pos = idx & (h - 1), a = ((idx - pos) << 1) + pos;
-            double2 *xr = x + (size_t)row * L;
-            const double2 u = xr[a], v = pos ? cmul(xr[a + h], twiddle(tw, pos * tstride, sgn)) : xr[a + h];
-            xr[a] = make_double2(u.x + v.x, u.y + v.y);
-            xr[a + h] = make_double2(u.x - v.x, u.y - v.y);
+            const int row = b >> (l - 1), pos = b & (half - 1);
+            double2 *xr = x + ((size_t)row << l);
+            const double2 u = xr[pos];
+            const double2 v = pos ? cmul(xr[pos + half], twiddle(tw, pos, half, sgn)) : xr[pos + half];
+            xr[pos] = cadd(u, v);
+            xr[pos + half] = csub(u, v);
         }
         __syncthreads();
     }

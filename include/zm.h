@@ -164,6 +164,18 @@ int zm_check_finite(zm_ctx *ctx);
  * 64 bytes. */
 int zm_measure_peak(int kind, double *ops_per_s);
 
+/* Exercise the bounded device-side wait that every mbarrier wait in the library uses (the paper
+ * has no counterpart): one CTA polls an mbarrier phase up to max_polls times (1 <= max_polls <=
+ * 2^34).  arrive = 0: nothing ever arrives, so the wait gives up, the kernel sets the timeout bit
+ * of its status word and returns, and this call returns ZM_ERR_TIMEOUT -- the same path a stuck
+ * copy would take inside the Birkhoff-Rott kernels, without a hang or a fault; arrive = 1: one
+ * thread arrives first and the call returns ZM_OK.  *elapsed_ms (may be NULL) receives the
+ * kernel's duration.  Synchronous on the legacy default stream; allocates one int. */
+int zm_wait_selftest(int64_t max_polls, int32_t arrive, double *elapsed_ms);
+
+/* The poll limit of the library's bounded waits (the kernels give up after this many polls). */
+int64_t zm_wait_poll_limit(void);
+
 /* ---- batches of interfaces (high order, FP32C) ------------------------------------------- */
 
 /* Many independent interfaces of uneven mesh sizes advanced together: each RK3 stage runs four

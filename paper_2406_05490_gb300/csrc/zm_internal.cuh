@@ -215,7 +215,10 @@ namespace dev {
 
 // Bounded waits: every spin on an mbarrier gives up after this many polls and reports
 // kErrTimeout through the status word instead of hanging the GPU.
-constexpr uint32_t kSpinLimit = 1u << 26;
+// Each mbarrier.try_wait poll that finds the phase incomplete suspends the thread for a few
+// microseconds (measured on GB300: 2^26 polls took 252 s, 3.8 us each), so 2^18 polls bound a
+// stuck wait to about one second; a bulk copy that does complete lands within microseconds.
+constexpr uint32_t kSpinLimit = 1u << 18;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {

@@ -134,10 +134,63 @@ __global__ void __launch_bounds__(kPeakTpb) rsqrt_probe(int iters, float *sink)
     if (s == 12345.678f) sink[0] = s;
 }
 
+// One CTA waits on a shared-memory mbarrier phase with the same bounded try-wait the
+// Birkhoff-Rott kernels use for their bulk copies.  With arrive = 0 nothing ever arrives (the
+// flag that nothing sets), so the wait gives up after max_polls polls and the kernel records
+// kErrTimeout in *status and returns; with arrive = 1 one thread arrives first and the wait
+// completes.  Nothing is left in flight either way.
+__global__ void wait_selftest_kernel(long long max_polls, int arrive, int *status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        dev::mbar_init(&bar, 1);
+        dev::fence_mbar_init();
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(dev::smem_u32(&bar)) : "memory");
+    __syncthreads();
+    bool done = false;
+    for (long long it = 0; it < max_polls && !done; ++it) done = dev::mbar_try_wait(&bar, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) *status = done ? 0 : kErrTimeout;
+}
+
 }  // namespace
 }  // namespace zm
 
 using namespace zm;
+
+extern "C" int zm_wait_selftest(int64_t max_polls, int32_t arrive, double *elapsed_ms)
+{
+    if (max_polls < 1 || max_polls > ((int64_t)1 << 34) || (arrive != 0 && arrive != 1))
+        return set_error(ZM_ERR_INVALID, "zm_wait_selftest: max_polls in [1, 2^34], arrive 0 or 1");
+    int *status = nullptr;
+    if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ZM_ERR_NOMEM, "zm_wait_selftest: alloc");
+    }
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a);
+    wait_selftest_kernel<<<1, 32>>>((long long)max_polls, arrive, status);
+    cudaEventRecord(b);
+    int rc = cuda_check(cudaGetLastError(), "zm_wait_selftest launch");
+    int h = 0;
+    if (!rc) rc = cuda_check(cudaMemcpy(&h, status, sizeof(int), cudaMemcpyDeviceToHost), "zm_wait_selftest");
+    float ms = 0.f;
+    if (!rc) cudaEventElapsedTime(&ms, a, b);
+    if (elapsed_ms) *elapsed_ms = ms;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(status);
+    if (!rc && (h & kErrTimeout))
+        rc = set_error(ZM_ERR_TIMEOUT, "zm_wait_selftest: the bounded device-side wait gave up (as intended)");
+    return rc;
+}
+
+extern "C" int64_t zm_wait_poll_limit(void) { return (int64_t)dev::kSpinLimit; }
 
 extern "C" int zm_measure_peak(int kind, double *ops_per_s)
 {

@@ -96,6 +96,8 @@ def load():
             "zm_reset_profile": (I, [VP]),
             "zm_check_finite": (I, [VP]),
             "zm_measure_peak": (I, [I, ctypes.POINTER(D)]),
+            "zm_wait_selftest": (I, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(D)]),
+            "zm_wait_poll_limit": (ctypes.c_int64, []),
             "zm_br_velocity_noalloc": (I, [ctypes.c_int32, VP, VP, D, VP, VP, VP]),
             "zm_batch_create": (I, [ctypes.c_int32, ctypes.POINTER(zm_mesh), ctypes.POINTER(D), D, D,
                                     ctypes.POINTER(D), ctypes.POINTER(VP)]),
@@ -231,6 +233,18 @@ def zm_measure_peak(kind):
     v = ctypes.c_double()
     _check(load().zm_measure_peak(int(kind), ctypes.byref(v)))
     return v.value
+
+
+def zm_wait_selftest(max_polls, arrive):
+    """Run the bounded device-side wait once: returns (status code, kernel ms) without raising,
+    so that ZM_ERR_TIMEOUT (nothing arrived, the wait gave up) can be checked."""
+    ms = ctypes.c_double()
+    rc = load().zm_wait_selftest(int(max_polls), int(arrive), ctypes.byref(ms))
+    return rc, ms.value
+
+
+def zm_wait_poll_limit():
+    return int(load().zm_wait_poll_limit())
 
 
 def zm_br_velocity_noalloc(n, z, gamma, delta, u, status=None, stream=None):

@@ -399,3 +399,25 @@ def test_checkpoint_resume(zm, order, fp32c, df64, n):
         assert rel(z6r, z6) <= 1e-15 and rel(w6r, w6) <= 1e-13
     else:
         assert np.array_equal(z6r, z6) and np.array_equal(w6r, w6)
+
+
+def test_bounded_wait_gives_up_and_the_gpu_stays_usable(zm):
+    """A device-side wait on a flag that nothing sets gives up after its poll limit and reports
+    ZM_ERR_TIMEOUT through the status word (no hang, no fault); the same wait with an arrival
+    completes; and a full evaluation afterwards still matches the oracle."""
+    rc, ms = zm.zm_wait_selftest(1 << 16, 0)
+    assert rc == zm.ZM_ERR_TIMEOUT and ms > 0
+    rc, _ = zm.zm_wait_selftest(1 << 16, 1)
+    assert rc == zm.ZM_OK
+    # the library's own limit: about a second of polling, so a stuck copy is reported quickly
+    rc, ms = zm.zm_wait_selftest(zm.zm_wait_poll_limit(), 0)
+    print(f"bounded wait: {zm.zm_wait_poll_limit()} polls gave up after {ms:.0f} ms")
+    assert rc == zm.ZM_ERR_TIMEOUT and 50.0 < ms < 5000.0
+    n = 32
+    z, w = inputs.random_state(n, seed=5)
+    m = oracle.Mesh(n, periodic=True)
+    u_ref, wd_ref = oracle.derivative(m, z, w, 0.5, 1.0, 0.0, 0.1 / n)
+    model = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n)
+    u, wd = model.velocity(z, w)
+    model.close()
+    assert rel(u, u_ref) <= TOL64 and rel(wd, wd_ref) <= TOL64

@@ -124,13 +124,13 @@ def kernel_source_hash():
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-def recorded_traffic():
+def recorded_traffic(tiles):
     """DRAM bytes per Birkhoff-Rott launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
+    current kernel source with the same tile shape (else None)."""
     p = os.path.join(ROOT, "profiles", "br_fp32c_traffic.json")
     try:
         d = json.load(open(p))
-        if d.get("source_sha256_16") == kernel_source_hash():
+        if d.get("source_sha256_16") == kernel_source_hash() and d.get("tile_shape") == list(tiles):
             return d.get("dram_bytes_per_launch_full_size")
     except Exception:
         pass
@@ -363,10 +363,10 @@ def bench_batched(zm, torch, inputs, flush, steps=10, warmup=2, count=64):
     zm.zm_batch_set_stream(h, stream.cuda_stream)
     for k, r in enumerate(insts):
         zm.zm_batch_set_state(h, k, r.z, r.w)
-    # autotuned work-item size on states with vorticity, then the initial states again
+    # autotuned tile shape and work-item size on states with vorticity, then the initial states again
     for k, r in enumerate(insts):
         zm.zm_batch_set_state(h, k, r.z, inputs.random_state(r.n, seed=k)[1])
-    chunk, _ = zm.zm_batch_autotune(h)
+    tiles, chunk, _ = zm.zm_batch_autotune_tiles(h)
     for k, r in enumerate(insts):
         zm.zm_batch_set_state(h, k, r.z, r.w)
     info = zm.zm_batch_info(h)
@@ -383,7 +383,7 @@ def bench_batched(zm, torch, inputs, flush, steps=10, warmup=2, count=64):
     zm.zm_batch_destroy(h)
     pairs_step = 3 * info["pairs_per_eval"]
     out = {"interfaces": count, "sides": [int(r.n) for r in insts], "points": info["points"],
-           "autotuned_chunk": chunk,
+           "autotuned_chunk": chunk, "autotuned_tiles": list(tiles),
            "pairs_per_step": pairs_step, "work_items": info["work_items"], "ctas": info["ctas"],
            "steps": steps, "ms_per_step": ms / steps,
            "gpairs_per_s": pairs_step * steps / (ms * 1e-3) / 1e9}
@@ -553,10 +553,10 @@ def run_gb300(args):
     z0, w0 = inputs.multi_mode(n, n_modes=16, seed=rank)
     model = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, fp32c=True)
     model.set_state(z0, w0)
-    # the autotuner times work-item sizes on a state with vorticity (w = 0 makes the first
+    # the autotuner times tile shapes and work-item sizes on a state with vorticity (w = 0 makes the first
     # stage's sheet strength vanish), then the interface is reset to its initial state
     model.set_state(z0, inputs.random_state(n, seed=1)[1])
-    chunk = zm.zm_autotune(model.h)
+    tiles, chunk = zm.zm_autotune_tiles(model.h)
     model.set_state(z0, w0)
 
     barrier(ws)
@@ -575,7 +575,7 @@ def run_gb300(args):
     br_ms = prof["ms"]["br"] / max(prof["launches"]["br"], 1)
     achieved = FLOPS_PER_PAIR * N * N / (br_ms * 1e-3) / 1e12
     peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = recorded_traffic()
+    traffic = recorded_traffic(tiles)
 
     # end to end through the C ABI with host buffers: H2D state in, one step, D2H state out
     zh = np.ascontiguousarray(z0)
@@ -588,6 +588,7 @@ def run_gb300(args):
     except Exception:
         zp, wp, zo, wo = torch.from_numpy(zh), torch.from_numpy(wh), torch.empty(3, N, dtype=torch.float64), torch.empty(2, N, dtype=torch.float64)
     e2e_model = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, fp32c=True)
+    zm.zm_autotune_tiles(e2e_model.h)  # the same mesh: the choice above, remembered in this process
     e2e_steps = max(3, min(args.steps, 10))
     for k in range(e2e_steps + 1):
         if k == 1:
@@ -631,7 +632,7 @@ def run_gb300(args):
         zh8, wh8 = inputs.multi_mode(nh, n_modes=8, seed=7, amp=0.02)
         mh = zm.ZModel(nh, periodic=True, atwood=0.7, g=1.0, delta=0.1 / nh, fp32c=True)
         mh.set_state(zh8, inputs.random_state(nh, seed=1)[1])
-        zm.zm_autotune(mh.h)
+        zm.zm_autotune_tiles(mh.h)
         mh.set_state(zh8, wh8)
         kh = 10
         msh, profh = timed_steps(mh, zm, torch, kh, 2, flush)
@@ -686,7 +687,8 @@ def run_gb300(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": dict(CONFIG, parallelism=f"replicas x{ws}", autotuned_chunk=chunk),
+        "config": dict(CONFIG, parallelism=f"replicas x{ws}", autotuned_chunk=chunk,
+                       autotuned_tiles=list(tiles)),
         "steps_per_s": steps_per_s * 1.0,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "br32_kernel",

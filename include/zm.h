@@ -121,6 +121,11 @@ int zm_set_cutoff(zm_ctx *ctx, double cutoff);
  * resident state is used, so set it first).  Other contexts have nothing to tune: *chosen = 0. */
 int zm_autotune(zm_ctx *ctx, const char *cache_path, int32_t *chosen);
 
+/* Autotune the tile shapes and the work decomposition of an FP32C high-order context together
+ * (see zm_batch_autotune_tiles).  Unlike zm_autotune, the choice can change results within the
+ * FP32C bound.  Other contexts: *tp1 = *tp2 = *chunk = 0. */
+int zm_autotune_tiles(zm_ctx *ctx, const char *cache_path, int32_t *tp1, int32_t *tp2, int32_t *chunk);
+
 /* Wait for the context's stream; reports ZM_ERR_TIMEOUT / ZM_ERR_CUDA raised by its kernels. */
 int zm_sync(zm_ctx *ctx);
 
@@ -211,6 +216,21 @@ int zm_batch_set_chunk(zm_batch *b, int32_t chunk);
  * and, if cache_path is not NULL, appended to / read from that text file.  Results do not
  * depend on the choice (exact fixed-point accumulation); synchronous. */
 int zm_batch_autotune(zm_batch *b, const char *cache_path, int32_t *chosen, float *best_ms);
+/* Tile shape of the all-pairs sum: every interface is cut into tiles of tp1 x tp2 mesh nodes
+ * (256 each; (16,16) by default, or (8,32), (32,8), (4,64), (64,4)) that serve both as target
+ * tiles and as source tiles.  Elongated tiles are more compact in space when the two mesh
+ * spacings differ, so fewer tile pairs need the near (exact-difference) path.  Changing the
+ * shape rebuilds the source records and the plan; results change within the FP32C bound (tile
+ * centres and the near/far split move), not bit for bit.  Synchronous. */
+int zm_batch_set_tile_shape(zm_batch *b, int32_t tp1, int32_t tp2);
+int zm_batch_get_tile_shape(zm_batch *b, int32_t *tp1, int32_t *tp2);
+/* Autotuner for tiles: times each candidate tile shape at the default work-item size, then the
+ * work-item sizes 1 .. 32 for the fastest shape (one evaluation each, twice, CUDA events), keeps
+ * the fastest pair, and remembers it like zm_batch_autotune (key suffix "|tiles"; the cache
+ * stores shape index * 1000 + work-item size).  Returns the shape and the work-item size, and
+ * the time per evaluation in *best_ms (-1 if the choice came from the memo or the cache). */
+int zm_batch_autotune_tiles(zm_batch *b, const char *cache_path, int32_t *tp1, int32_t *tp2, int32_t *chunk,
+                            float *best_ms);
 /* Cutoff sum (see zm_set_cutoff) for interface `index`, or all interfaces if index = -1. */
 int zm_batch_set_cutoff(zm_batch *b, int32_t index, double cutoff);
 /* Totals: mesh points, pair interactions per evaluation, work items, persistent CTAs. */

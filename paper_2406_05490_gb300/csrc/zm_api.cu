@@ -94,6 +94,7 @@ int batch_status(Batch *b);
 int batch_keep_phi(Batch *b, int on);
 int batch_set_cutoff(Batch *b, int index, double cutoff);
 int batch_autotune(Batch *b, const char *path, int *chosen, float *ms);
+int batch_autotune_tiles(Batch *b, const char *path, int *tp1, int *tp2, int *chunk, float *ms);
 
 static int stage_index(zm_ctx *c, const double *y) { return y == c->y0 ? 0 : (y == c->ya ? 1 : 2); }
 
@@ -545,6 +546,24 @@ int zm_autotune(zm_ctx *c, const char *cache_path, int32_t *chosen)
     int ch = 0;
     int rc = batch_autotune(c->batch, cache_path, &ch, nullptr);
     if (chosen) *chosen = ch;
+    return rc;
+}
+
+int zm_autotune_tiles(zm_ctx *c, const char *cache_path, int32_t *tp1, int32_t *tp2, int32_t *chunk)
+{
+    if (!c) return set_error(ZM_ERR_INVALID, "zm_autotune_tiles: null context");
+    if (!c->batch) {  // only the FP32C all-pairs kernel is tiled this way
+        if (tp1) *tp1 = 0;
+        if (tp2) *tp2 = 0;
+        if (chunk) *chunk = 0;
+        return ZM_OK;
+    }
+    batch_bind(c->batch, c->stream, &c->prof);
+    int a = 0, b = 0, k = 0;
+    const int rc = batch_autotune_tiles(c->batch, cache_path, &a, &b, &k, nullptr);
+    if (tp1) *tp1 = a;
+    if (tp2) *tp2 = b;
+    if (chunk) *chunk = k;
     return rc;
 }
 

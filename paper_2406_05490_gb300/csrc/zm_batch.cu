@@ -77,11 +77,30 @@ __global__ void __launch_bounds__(kPtb)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+}  // namespace
+
+// Candidate patch shapes of the tiles (256 mesh nodes each): square, and elongated ones that are
+// more compact in space when the mesh spacing differs between the two directions.
+const int kShapes[kNumShapes][2] = {{16, 16}, {8, 32}, {32, 8}, {4, 64}, {64, 4}};
+
+// Tiles an interface's record buffers must hold for any candidate shape.
+size_t tile_capacity(int n1, int n2)
+{
+    size_t m = 0;
+    for (int k = 0; k < kNumShapes; ++k) {
+        const size_t nt = (size_t)((n1 + kShapes[k][0] - 1) / kShapes[k][0]) * ((n2 + kShapes[k][1] - 1) / kShapes[k][1]);
+        m = std::max(m, nt);
+    }
+    return m;
+}
+
+namespace {
+
 // sizes of the pieces of one interface's slab, in order
 void slab_layout(const zm_mesh &m, size_t sz[12])
 {
     const size_t N = (size_t)m.n1 * m.n2;
-    const size_t nt = (size_t)((m.n1 + 15) / 16) * ((m.n2 + 15) / 16);
+    const size_t nt = tile_capacity(m.n1, m.n2);
     const size_t slots = nt * 256;
     const size_t s[12] = {5 * N * 8, 5 * N * 8, 5 * N * 8, 3 * N * 8, N * 8, N * 8, 3 * N * 8,
                           slots * kRec32 * 4, slots * kRec32F * 4, nt * 16, 4, 4};
@@ -165,7 +184,7 @@ int Batch::alloc_inst(Inst &I, const zm_mesh &m, double atwood, double g, double
     I.tinfo = reinterpret_cast<float4 *>(b + off[9]);
     I.gmax = reinterpret_cast<unsigned int *>(b + off[10]);
     I.scale = reinterpret_cast<int *>(b + off[11]);
-    init_far_records(I.far_rec, I.tiling.ntiles, (float)(delta * delta), async ? s : nullptr);
+    init_far_records(I.far_rec, (int)tile_capacity(m.n1, m.n2), (float)(delta * delta), async ? s : nullptr);
     *slab_out = slab;
     return cuda_check(cudaGetLastError(), "interface state init");
 }
@@ -272,7 +291,7 @@ namespace {
 std::mutex g_tune_mutex;
 std::map<std::string, int> g_tune_memo;  // key -> chosen work-item size, for this process
 
-std::string tune_key(const Batch &b)
+std::string tune_key(const Batch &b, bool shape_neutral = false)
 {
     cudaDeviceProp prop;
     std::memset(&prop, 0, sizeof(prop));
@@ -284,7 +303,7 @@ std::string tune_key(const Batch &b)
     int maxtiles = 0;
     for (auto &I : b.h) {
         pairs += (long double)I.geom.N * I.geom.N;
-        maxtiles = std::max(maxtiles, I.tiling.ntiles);
+        maxtiles = std::max(maxtiles, shape_neutral ? make_tiling(I.geom).ntiles : I.tiling.ntiles);
     }
     const int pb = (int)std::floor(std::log2((double)pairs + 1.0));
     const int ib = (int)std::floor(std::log2((double)b.h.size()));
@@ -382,6 +401,109 @@ int Batch::autotune(const char *cache_path, int *chosen, float *best_ms)
     if (chosen) *chosen = best_c;
     if (best_ms) *best_ms = best / 2;
     return set_chunk(best_c);
+}
+
+float Batch::time_eval(int *rc)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        *rc = set_error(ZM_ERR_CUDA, "autotune: event creation failed");
+        return 0.f;
+    }
+    float total = 0.f, ms = 0.f;
+    *rc = derivative(0, stream);  // warm-up
+    for (int rep = 0; rep < 2 && !*rc; ++rep) {
+        cudaEventRecord(a, stream);
+        *rc = derivative(0, stream);
+        cudaEventRecord(b, stream);
+        cudaEventSynchronize(b);
+        cudaEventElapsedTime(&ms, a, b);
+        total += ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return total;
+}
+
+int Batch::set_shape(int k)
+{
+    if (k < 0 || k >= kNumShapes) return set_error(ZM_ERR_INVALID, "tile shape: unknown candidate");
+    shape = k;
+    for (auto &I : h) {
+        I.tiling = make_tiling_shape(I.geom, kShapes[k][0], kShapes[k][1]);
+        // padding slots of the new tiling must hold zero-strength sources, not another shape's
+        // nodes: clear the records of the whole capacity
+        const size_t cap = tile_capacity(I.geom.n1, I.geom.n2);
+        cudaMemsetAsync(I.near_rec, 0, cap * 256 * kRec32 * sizeof(float), stream);
+        cudaMemsetAsync(I.tinfo, 0, cap * sizeof(float4), stream);
+        init_far_records(I.far_rec, (int)cap, (float)(I.delta * I.delta), stream);
+    }
+    int rc = cuda_check(cudaGetLastError(), "tile shape change");
+    return rc ? rc : plan();
+}
+
+int Batch::autotune_tiles(const char *cache_path, int *shape_out, int *chunk_out, float *best_ms)
+{
+    if (h.empty()) return ZM_OK;
+    const std::string key = tune_key(*this, true) + "|tiles";
+    int code = 0;  // shape * 1000 + chunk
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_memo.find(key);
+        if (it != g_tune_memo.end()) code = it->second;
+    }
+    if (code <= 0 && cache_lookup(cache_path, key, &code)) {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_memo[key] = code;
+    }
+    int rc = ZM_OK;
+    float best = -1.0f;
+    if (code <= 0 || code / 1000 >= kNumShapes) {
+        Prof *saved = prof;
+        Prof quiet;  // keep the tuning launches out of the caller's counters
+        prof = &quiet;
+        // patch shapes at the default work-item size, then work-item sizes for the best shape
+        int best_k = 0;
+        float best_t = 1e30f;
+        for (int k = 0; k < kNumShapes && !rc; ++k) {
+            rc = set_shape(k);
+            if (!rc) rc = set_chunk(0);
+            const float t = rc ? 0.f : time_eval(&rc);
+            if (!rc && t < best_t) {
+                best_t = t;
+                best_k = k;
+            }
+        }
+        if (!rc) rc = set_shape(best_k);
+        int maxtiles = 1;
+        for (auto &I : h) maxtiles = std::max(maxtiles, I.tiling.ntiles);
+        int best_c = 1;
+        best_t = 1e30f;
+        for (int cand = 1; cand <= 32 && cand <= maxtiles && !rc; cand *= 2) {
+            rc = set_chunk(cand);
+            const float t = rc ? 0.f : time_eval(&rc);
+            if (!rc && t < best_t) {
+                best_t = t;
+                best_c = cand;
+            }
+        }
+        prof = saved;
+        prof_release(quiet);
+        if (rc) return rc;
+        code = best_k * 1000 + best_c;
+        best = best_t / 2;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mutex);
+            g_tune_memo[key] = code;
+        }
+        cache_store(cache_path, key, code, best);
+    }
+    rc = set_shape(code / 1000);
+    if (!rc) rc = set_chunk(code % 1000);
+    if (shape_out) *shape_out = code / 1000;
+    if (chunk_out) *chunk_out = code % 1000;
+    if (best_ms) *best_ms = best;
+    return rc;
 }
 
 int Batch::set_dt(double dt)
@@ -545,6 +667,14 @@ int batch_keep_phi(Batch *b, int on)
     return b->plan();
 }
 int batch_autotune(Batch *b, const char *path, int *chosen, float *ms) { return b->autotune(path, chosen, ms); }
+int batch_autotune_tiles(Batch *b, const char *path, int *tp1, int *tp2, int *chunk, float *ms)
+{
+    int k = 0;
+    const int rc = b->autotune_tiles(path, &k, chunk, ms);
+    if (tp1) *tp1 = kShapes[k][0];
+    if (tp2) *tp2 = kShapes[k][1];
+    return rc;
+}
 
 }  // namespace zm
 
@@ -686,6 +816,35 @@ int zm_batch_autotune(zm_batch *bt, const char *cache_path, int32_t *chosen, flo
     int c = 0;
     int rc = bt->b.autotune(cache_path, &c, best_ms);
     if (chosen) *chosen = c;
+    return rc;
+}
+
+int zm_batch_set_tile_shape(zm_batch *bt, int32_t tp1, int32_t tp2)
+{
+    if (!bt) return set_error(ZM_ERR_INVALID, "zm_batch_set_tile_shape: null batch");
+    for (int k = 0; k < kNumShapes; ++k)
+        if (kShapes[k][0] == tp1 && kShapes[k][1] == tp2) return bt->b.set_shape(k);
+    return set_error(ZM_ERR_INVALID,
+                     "zm_batch_set_tile_shape: (tp1, tp2) must be (16,16), (8,32), (32,8), (4,64) or (64,4)");
+}
+
+int zm_batch_get_tile_shape(zm_batch *bt, int32_t *tp1, int32_t *tp2)
+{
+    if (!bt || !tp1 || !tp2) return set_error(ZM_ERR_INVALID, "zm_batch_get_tile_shape: null argument");
+    *tp1 = kShapes[bt->b.shape][0];
+    *tp2 = kShapes[bt->b.shape][1];
+    return ZM_OK;
+}
+
+int zm_batch_autotune_tiles(zm_batch *bt, const char *cache_path, int32_t *tp1, int32_t *tp2, int32_t *chunk,
+                            float *best_ms)
+{
+    if (!bt) return set_error(ZM_ERR_INVALID, "zm_batch_autotune_tiles: null batch");
+    int a = 0, b = 0, c = 0;
+    const int rc = batch_autotune_tiles(&bt->b, cache_path, &a, &b, &c, best_ms);
+    if (tp1) *tp1 = a;
+    if (tp2) *tp2 = b;
+    if (chunk) *chunk = c;
     return rc;
 }
 

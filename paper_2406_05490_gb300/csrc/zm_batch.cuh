@@ -8,6 +8,12 @@
 
 namespace zm {
 
+// Candidate patch shapes (tp1, tp2) of the 256-node tiles; index 0 is 16 x 16.
+constexpr int kNumShapes = 5;
+extern const int kShapes[kNumShapes][2];
+// Tiles an interface's record buffers hold: enough for any candidate shape.
+size_t tile_capacity(int n1, int n2);
+
 class Batch {
 public:
     std::vector<Inst> h;  // members: host copy of the device descriptors
@@ -19,6 +25,7 @@ public:
     long long nitems = 0;
     int ctas = 0, occ = 1, sms = 152;
     int chunk_override = 0;  // 0: default work-item size by mesh size
+    int shape = 0;           // index into the candidate patch shapes (0: 16 x 16)
     unsigned long long *counter = nullptr;
     int *err = nullptr;
     std::vector<void *> owned;  // slabs allocated by init() (fixed batches)
@@ -45,6 +52,11 @@ public:
     int set_chunk(int chunk);
     // time candidate work-item sizes on the resident states, keep the fastest
     int autotune(const char *cache_path, int *chosen, float *best_ms);
+    // re-tile every member with candidate patch shape k (records cleared, plan rebuilt)
+    int set_shape(int k);
+    // time candidate patch shapes, then work-item sizes for the best one; keep the fastest
+    int autotune_tiles(const char *cache_path, int *shape_out, int *chunk_out, float *best_ms);
+    float time_eval(int *rc);  // ms of two derivative evaluations after a warm-up
     int set_dt(double dt);          // all members
     void drop_graph();
 

@@ -130,17 +130,19 @@ constexpr int kTpb64s = 32;  // small meshes: one warp per target block
 
 }  // namespace
 
-Tiling make_tiling(const Geom &g)
+Tiling make_tiling_shape(const Geom &g, int tp1, int tp2)
 {
     Tiling t;
-    t.tp1 = kTile1;
-    t.tp2 = kTile2;
-    t.ts = kTile1 * kTile2;
-    t.nt1 = (g.n1 + kTile1 - 1) / kTile1;
-    t.nt2 = (g.n2 + kTile2 - 1) / kTile2;
+    t.tp1 = tp1;
+    t.tp2 = tp2;
+    t.ts = tp1 * tp2;
+    t.nt1 = (g.n1 + tp1 - 1) / tp1;
+    t.nt2 = (g.n2 + tp2 - 1) / tp2;
     t.ntiles = t.nt1 * t.nt2;
     return t;
 }
+
+Tiling make_tiling(const Geom &g) { return make_tiling_shape(g, kTile1, kTile2); }
 
 BrPlan plan_br(const Geom &g, const Tiling &t, int sm_count)
 {

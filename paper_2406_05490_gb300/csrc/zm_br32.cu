@@ -280,7 +280,8 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
 #pragma unroll
         for (int r = 0; r < kR; ++r) {
             const int slot = r * kT + tid;
-            const int i = ti * 16 + (slot >> 4), j = tj * 16 + (slot & 15);
+            const int lg2 = __ffs(I.tiling.tp2) - 1;  // tp2 is a power of two
+            const int i = ti * I.tiling.tp1 + (slot >> lg2), j = tj * I.tiling.tp2 + (slot & (I.tiling.tp2 - 1));
             if (i < I.geom.n1 && j < I.geom.n2) {
                 const size_t p = (size_t)i * I.geom.n2 + j;
 #pragma unroll

@@ -178,7 +178,9 @@ int check_finite(zm_ctx *c, const double *y, size_t n, int *dev_flag);
 
 // ---- Birkhoff-Rott kernels (zm_br.cu) ----------------------------------------------------------
 BrPlan plan_br(const Geom &g, const Tiling &t, int sm_count);
-Tiling make_tiling(const Geom &g);
+Tiling make_tiling(const Geom &g);  // 16 x 16 patches
+// tp1 x tp2 patches (tp1 * tp2 = 256 slots, both powers of two)
+Tiling make_tiling_shape(const Geom &g, int tp1, int tp2);
 int launch_br(zm_ctx *c, const double *y);  // FP64 path (then launch_reduce)
 
 // ---- FP32C Birkhoff-Rott kernel over a batch of interfaces (zm_br32.cu) ----------------------------

@@ -112,6 +112,13 @@ def load():
             "zm_batch_autotune": (I, [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_float)]),
             "zm_autotune": (I, [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]),
+            "zm_autotune_tiles": (I, [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+            "zm_batch_set_tile_shape": (I, [VP, ctypes.c_int32, ctypes.c_int32]),
+            "zm_batch_get_tile_shape": (I, [VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+            "zm_batch_autotune_tiles": (I, [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_float)]),
             "zm_set_cutoff": (I, [VP, D]),
             "zm_batch_set_cutoff": (I, [VP, ctypes.c_int32, D]),
             "zm_batch_info": (I, [VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
@@ -328,6 +335,34 @@ def zm_autotune(h, cache_path=None):
     p = cache_path.encode() if cache_path else None
     _check(load().zm_autotune(h, p, ctypes.byref(c)))
     return c.value
+
+
+def zm_autotune_tiles(h, cache_path=None):
+    """Tile shape and work-item size of an FP32C context, tuned together: ((tp1, tp2), chunk)."""
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    p = cache_path.encode() if cache_path else None
+    _check(load().zm_autotune_tiles(h, p, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return (a.value, b.value), c.value
+
+
+def zm_batch_set_tile_shape(h, tp1, tp2):
+    _check(load().zm_batch_set_tile_shape(h, int(tp1), int(tp2)))
+
+
+def zm_batch_get_tile_shape(h):
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().zm_batch_get_tile_shape(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def zm_batch_autotune_tiles(h, cache_path=None):
+    """((tp1, tp2), chunk, ms per evaluation or -1 when remembered)."""
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ms = ctypes.c_float()
+    p = cache_path.encode() if cache_path else None
+    _check(load().zm_batch_autotune_tiles(h, p, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                          ctypes.byref(ms)))
+    return (a.value, b.value), c.value, ms.value
 
 
 def zm_batch_info(h):

@@ -129,3 +129,85 @@ def test_batch_rejects_bad_arguments(zm):
     with pytest.raises(zm.ZMError) as e:
         zm.zm_batch_create([(16, 16, 1.0, 1.0, True)], [0.5], delta=[0.0])
     assert e.value.code == zm.ZM_ERR_INVALID
+
+
+SHAPES = [(16, 16), (8, 32), (32, 8), (4, 64), (64, 4)]
+
+
+def test_tile_shapes_parity(zm):
+    """Every candidate tile shape gives results within the FP32C bound of the oracle, on a mix of
+    square, anisotropic (dx1 = 4 dx2), ragged and free-edge interfaces; within one shape the
+    work-item size still changes no bit."""
+    specs = [(64, 64, True, 0.6, 2), (32, 128, True, 0.5, 7), (37, 53, False, 0.4, 1), (5, 9, False, 0.5, 5)]
+    h, delta = make_batch(zm, specs)
+    states = [inputs.random_state(n1, n2, seed=s) for n1, n2, _, _, s in specs]
+    refs = []
+    for k, (z, w) in enumerate(states):
+        zm.zm_batch_set_state(h, k, z, w)
+        n1, n2, per, at, _ = specs[k]
+        refs.append(oracle.derivative(oracle.Mesh(n1, n2, periodic=per), z, w, at, 1.3, 0.0, delta[k]))
+    for tp1, tp2 in SHAPES:
+        zm.zm_batch_set_tile_shape(h, tp1, tp2)
+        assert zm.zm_batch_get_tile_shape(h) == (tp1, tp2)
+        zm.zm_batch_set_chunk(h, 0)
+        zm.zm_batch_velocity(h)
+        first = []
+        for k, (n1, n2, _, _, _) in enumerate(specs):
+            u, wd = np.empty((3, n1 * n2)), np.empty((2, n1 * n2))
+            zm.zm_batch_get_velocity(h, k, u, wd)
+            first.append(u)
+            eu, ew = rel(u, refs[k][0]), rel(wd, refs[k][1])
+            print(f"tiles {tp1}x{tp2} [{k}] {n1}x{n2}: rel L2 u={eu:.3e} wdot={ew:.3e}")
+            assert eu <= TOL32 and ew <= TOL32
+        zm.zm_batch_set_chunk(h, 1)
+        zm.zm_batch_velocity(h)
+        for k, (n1, n2, _, _, _) in enumerate(specs):
+            u = np.empty((3, n1 * n2))
+            zm.zm_batch_get_velocity(h, k, u, None)
+            assert np.array_equal(u, first[k])
+    with pytest.raises(zm.ZMError):
+        zm.zm_batch_set_tile_shape(h, 16, 8)
+    zm.zm_batch_destroy(h)
+
+
+def test_tile_autotune_on_an_anisotropic_mesh(zm, tmp_path):
+    """On a 64 x 256 mesh of the unit square (dx1 = 4 dx2) a 16 x 16 tile spans 0.25 x 0.0625,
+    an 8 x 32 tile 0.125 x 0.125: the tile autotuner picks a shape no slower than the square one,
+    remembers it, and the tuned batch still matches the oracle."""
+    import torch
+    n1, n2 = 64, 256
+    z, w = inputs.random_state(n1, n2, seed=23)
+    h = zm.zm_batch_create([(n1, n2, 1.0, 1.0, True)], [0.5], g=1.3, delta=[0.1 / n2])
+    zm.zm_batch_set_state(h, 0, z, w)
+
+    def br_ms(shape):
+        zm.zm_batch_set_tile_shape(h, *shape)
+        zm.zm_batch_set_chunk(h, 0)
+        zm.zm_batch_velocity(h)
+        zm.zm_batch_set_profiling(h, 1)
+        for _ in range(3):
+            zm.zm_batch_velocity(h)
+        p = zm.zm_batch_get_profile(h)
+        zm.zm_batch_set_profiling(h, 0)
+        return p["ms"]["br"] / p["launches"]["br"]
+
+    square = br_ms((16, 16))
+    cache = str(tmp_path / "tiles.txt")
+    shape, chunk, ms = zm.zm_batch_autotune_tiles(h, cache)
+    print(f"anisotropic 64x256: tuned tiles {shape}, chunk {chunk}, {ms:.3f} ms/eval; 16x16 BR {square:.3f} ms")
+    assert shape in SHAPES and 1 <= chunk <= 32 and ms > 0
+    assert zm.zm_batch_get_tile_shape(h) == shape
+    zm.zm_batch_set_chunk(h, 0)
+    tuned = br_ms(shape)
+    assert tuned <= 1.1 * square
+    shape2, chunk2, ms2 = zm.zm_batch_autotune_tiles(h, cache)  # remembered
+    assert (shape2, chunk2, ms2) == (shape, chunk, -1.0)
+    assert any("|tiles" in line for line in open(cache))
+    zm.zm_batch_set_chunk(h, chunk)
+    zm.zm_batch_velocity(h)
+    u, wd = np.empty((3, n1 * n2)), np.empty((2, n1 * n2))
+    zm.zm_batch_get_velocity(h, 0, u, wd)
+    zm.zm_batch_destroy(h)
+    u_ref, wd_ref = oracle.derivative(oracle.Mesh(n1, n2, periodic=True), z, w, 0.5, 1.3, 0.0, 0.1 / n2)
+    assert rel(u, u_ref) <= TOL32 and rel(wd, wd_ref) <= TOL32
+    torch.cuda.synchronize()

@@ -208,6 +208,17 @@ def test_tile_autotune_on_an_anisotropic_mesh(zm, tmp_path):
     u, wd = np.empty((3, n1 * n2)), np.empty((2, n1 * n2))
     zm.zm_batch_get_velocity(h, 0, u, wd)
     zm.zm_batch_destroy(h)
-    u_ref, wd_ref = oracle.derivative(oracle.Mesh(n1, n2, periodic=True), z, w, 0.5, 1.3, 0.0, 0.1 / n2)
-    assert rel(u, u_ref) <= TOL32 and rel(wd, wd_ref) <= TOL32
+    mesh = oracle.Mesh(n1, n2, periodic=True)
+    u_ref, wd_ref = oracle.derivative(mesh, z, w, 0.5, 1.3, 0.0, 0.1 / n2)
+    # dw/dt differentiates |u|^2/2 with the 1/dx2 = 256 stencil: on this random state, velocity
+    # errors of relative size e that are uncorrelated between nodes reach dw/dt amplified about
+    # 13-fold.  The bound is that amplification of the velocity bound, measured on the oracle
+    # with seeded noise of relative L2 size TOL32 added to its own velocity.
+    a1, a2, hm, _ = oracle.geometry(mesh, z)
+    noise = np.random.default_rng(0).standard_normal(u_ref.shape)
+    u_pert = u_ref + TOL32 * np.linalg.norm(u_ref) / np.linalg.norm(noise) * noise
+    wd_pert = oracle.wdot(mesh, oracle.phi(z, w, hm, u_pert, 1.3), w, 0.5, 0.0)
+    tol_wd = max(TOL32, rel(wd_pert, wd_ref))
+    print(f"anisotropic 64x256: rel L2 u={rel(u, u_ref):.3e} wdot={rel(wd, wd_ref):.3e} (bound {tol_wd:.2e})")
+    assert rel(u, u_ref) <= TOL32 and rel(wd, wd_ref) <= tol_wd
     torch.cuda.synchronize()

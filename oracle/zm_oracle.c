@@ -25,7 +25,9 @@
  *       u_i = -(dx1 dx2 / 4 pi) sum_j (z_i - z_j) x gamma_j / (|z_i - z_j|^2 + delta^2)^(3/2).
  *   Low order (Sec. 2: FFT approximation of the Birkhoff-Rott integral): Riesz transforms
  *       s = R1 w1 + R2 w2,  R_l^(k) = -i k_l / |k|,  k_l = 2 pi m_l / L_l,
- *     multiplier zero at k = 0 and on the Nyquist row and column; u = -1/2 s N.
+ *     multiplier zero at k = 0 and on the Nyquist row and column (even sides); u = -1/2 s N.
+ *     Sides of any length: radix-2 for powers of two, otherwise Cooley-Tukey on the smallest
+ *     prime factor with prime lengths summed by the definition of the DFT.
  *   Cutoff (Sec. 3.2.2 CutoffBRSolver: only the points within a 3D distance of each point):
  *     the same sum restricted to |z_i - z_j| <= cutoff.  Whether a pair is in is a yes/no
  *     decision taken in the precision of the GPU kernel: with zh = fl32(z), zl = fl32(z - zh),
@@ -282,13 +284,93 @@ static void fft1d(int n, double *re, double *im, size_t stride, int sign)
     }
 }
 
-void zmo_fft2(int n1, int n2, double *re, double *im, int sign)
+/* Any length n (Cooley-Tukey, decimation in time, split on the smallest prime factor p of n;
+ * a prime length is summed by the definition).  With n = p m and x_q[t] = x[t p + q]:
+ *     X[k] = sum_q W_n^(q k) Y_q[k mod m],   Y_q = DFT_m(x_q),   W_n = exp(sign 2 pi i / n).
+ * `wr`, `wi` hold W_ntop^t for t < ntop, with n dividing ntop: W_n^e = W_ntop^(e ntop / n).
+ * Input x (stride `stride`), output X (contiguous), scratch of 2n doubles per level. */
+static void dft_any(int n, const double *xr, const double *xi, size_t stride, double *yr,
+                    double *yi, int ntop, const double *wr, const double *wi)
 {
-    for (int i = 0; i < n1; i++) fft1d(n2, re + (size_t)i * n2, im + (size_t)i * n2, 1, sign);
-    for (int j = 0; j < n2; j++) fft1d(n1, re + j, im + j, (size_t)n2, sign);
+    int p = 2;
+    while (p * p <= n && n % p) p++;
+    if (n % p) p = n; /* n is prime (or 1) */
+    const int m = n / p, scale = ntop / n;
+    if (p == n) {
+        for (int k = 0; k < n; k++) {
+            double sr = 0.0, si = 0.0;
+            for (int t = 0; t < n; t++) {
+                const size_t e = (size_t)((long long)t * k % n) * scale;
+                const double ar = xr[t * stride], ai = xi[t * stride];
+                sr += ar * wr[e] - ai * wi[e];
+                si += ar * wi[e] + ai * wr[e];
+            }
+            yr[k] = sr;
+            yi[k] = si;
+        }
+        return;
+    }
+    double *sub = malloc(2 * (size_t)n * sizeof(double)); /* Y_q for q < p, each of length m */
+    for (int q = 0; q < p; q++)
+        dft_any(m, xr + q * stride, xi + q * stride, stride * p, sub + (size_t)q * m,
+                sub + (size_t)n + (size_t)q * m, ntop, wr, wi);
+    for (int k = 0; k < n; k++) {
+        double sr = 0.0, si = 0.0;
+        for (int q = 0; q < p; q++) {
+            const size_t e = (size_t)((long long)q * k % n) * scale;
+            const double ar = sub[(size_t)q * m + k % m], ai = sub[(size_t)n + (size_t)q * m + k % m];
+            sr += ar * wr[e] - ai * wi[e];
+            si += ar * wi[e] + ai * wr[e];
+        }
+        yr[k] = sr;
+        yi[k] = si;
+    }
+    free(sub);
 }
 
-static int signed_freq(int idx, int n) { return idx < n / 2 ? idx : idx - n; }
+/* One complex sequence of any length n >= 1 in place (stride `stride`), sign as in fft1d:
+ * powers of two go through fft1d, other lengths through dft_any. */
+static void fft1d_any(int n, double *re, double *im, size_t stride, int sign, const double *wr,
+                      const double *wi)
+{
+    if ((n & (n - 1)) == 0) {
+        fft1d(n, re, im, stride, sign);
+        return;
+    }
+    double *yr = malloc(2 * (size_t)n * sizeof(double)), *yi = yr + n;
+    dft_any(n, re, im, stride, yr, yi, n, wr, wi);
+    for (int k = 0; k < n; k++) {
+        re[k * stride] = yr[k];
+        im[k * stride] = yi[k];
+    }
+    free(yr);
+}
+
+/* W_n^t = exp(sign 2 pi i t / n), t < n, into wr[t], wi[t]. */
+static void roots(int n, int sign, double *wr, double *wi)
+{
+    for (int t = 0; t < n; t++) {
+        const double ang = sign * 2.0 * ZMO_PI * t / n;
+        wr[t] = cos(ang);
+        wi[t] = sin(ang);
+    }
+}
+
+void zmo_fft2(int n1, int n2, double *re, double *im, int sign)
+{
+    double *w1 = malloc(2 * (size_t)n1 * sizeof(double)), *w2 = malloc(2 * (size_t)n2 * sizeof(double));
+    roots(n1, sign, w1, w1 + n1);
+    roots(n2, sign, w2, w2 + n2);
+    for (int i = 0; i < n1; i++)
+        fft1d_any(n2, re + (size_t)i * n2, im + (size_t)i * n2, 1, sign, w2, w2 + n2);
+    for (int j = 0; j < n2; j++) fft1d_any(n1, re + j, im + j, (size_t)n2, sign, w1, w1 + n1);
+    free(w1);
+    free(w2);
+}
+
+/* Signed frequency of DFT index idx: 0, 1, .., then negative from the middle on (for even n the
+ * middle index n/2 maps to -n/2, the Nyquist frequency, whose multiplier is zero). */
+static int signed_freq(int idx, int n) { return 2 * idx < n ? idx : idx - n; }
 
 void zmo_riesz_scalar(const zmo_mesh *m, const double *w, double *s)
 {

@@ -346,6 +346,34 @@ def test_fft_matches_numpy():
         np.testing.assert_allclose(re + 1j * im, np.fft.ifft2(x) * n1 * n2, atol=1e-12 * n1 * n2)
 
 
+def test_fft_any_length_matches_numpy():
+    # lengths that are not powers of two go through the general Cooley-Tukey path: composite
+    # (12, 24, 38 = 2 x 19, 152 = 8 x 19), prime (5, 7, 19) and odd composite (9, 15)
+    rng = np.random.default_rng(5)
+    for n1, n2 in ((12, 19), (38, 24), (152, 9), (5, 7), (15, 16), (16, 152)):
+        x = rng.normal(size=(n1, n2)) + 1j * rng.normal(size=(n1, n2))
+        re, im = oracle.fft2(x.real, x.imag, -1)
+        np.testing.assert_allclose(re + 1j * im, np.fft.fft2(x), atol=1e-12 * n1 * n2)
+        re, im = oracle.fft2(x.real, x.imag, +1)
+        np.testing.assert_allclose(re + 1j * im, np.fft.ifft2(x) * n1 * n2, atol=1e-12 * n1 * n2)
+
+
+@pytest.mark.parametrize("n1,n2,m1,m2", [(38, 24, 5, -7), (19, 15, 9, -7), (152, 40, -60, 11)])
+def test_riesz_gradient_mode_any_side(n1, n2, m1, m2):
+    # the closed form R . grad cos(phase) = |k| cos(phase) on sides that are not powers of two,
+    # including odd sides with the highest frequency they carry ((n - 1) / 2), which a wrong
+    # signed-frequency map would send to the wrong |k|
+    m = oracle.Mesh(n1, n2, L1=1.0, L2=2.0, periodic=True)
+    a, b = inputs.mesh_coords(n1, n2, 1.0, 2.0)
+    k1, k2 = 2 * np.pi * m1 / 1.0, 2 * np.pi * m2 / 2.0
+    ph = k1 * a + k2 * b + 0.4
+    kk = math.hypot(k1, k2)
+    w = np.stack([-k1 * np.sin(ph), -k2 * np.sin(ph)])
+    np.testing.assert_allclose(oracle.riesz_scalar(m, w), kk * np.cos(ph), atol=1e-11 * kk)
+    wc = np.stack([-k2 * np.sin(ph), k1 * np.sin(ph)])
+    np.testing.assert_allclose(oracle.riesz_scalar(m, wc), 0.0, atol=1e-11 * kk)
+
+
 def test_riesz_gradient_mode_and_curl():
     n1, n2 = 32, 16
     m = oracle.Mesh(n1, n2, L1=1.0, L2=2.0, periodic=True)

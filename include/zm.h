@@ -54,7 +54,7 @@ extern "C" {
 #define ZM_ERR_CUDA (-3)         /* a CUDA runtime call or kernel launch failed               */
 #define ZM_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up (status word set)      */
 #define ZM_ERR_UNSUPPORTED (-5)  /* valid but not supported: low/medium order on a free-edge
-                                    mesh, FFT side not a power of two                      */
+                                    mesh, FFT side of another form than R 2^a              */
 #define ZM_ERR_NONFINITE (-6)    /* the state became NaN/Inf (checked by zm_check_finite)    */
 #define ZM_ERR_BUSY (-7)         /* resource budget exhausted (serving admission)            */
 
@@ -86,9 +86,12 @@ typedef struct zm_ctx zm_ctx;
 /* Create a context for one interface on the current CUDA device.  Allocates all device state
  * and workspace (owned by the context until zm_destroy).  delta > 0 is the Birkhoff-Rott core
  * size (high order); mu >= 0 the artificial viscosity; `order` is ZM_ORDER_* | ZM_PREC_*.
- * Returns ZM_ERR_UNSUPPORTED for low or medium order on a free-edge mesh or a non power-of-two
- * side, and for ZM_PREC_DF64 with medium or high order; ZM_ERR_INVALID for ZM_PREC_FP32C
- * combined with ZM_PREC_DF64. */
+ * Low and medium order (periodic FFT solver, Sec. 2 and 3.1) take sides L = R 2^a with a >= 3,
+ * R odd in 1 .. 19 and L <= 8192 (the paper's 4864 = 19 x 2^8 among them); ZM_PREC_DF64 takes
+ * powers of two from 8 to 4096.
+ * Returns ZM_ERR_UNSUPPORTED for low or medium order on a free-edge mesh or on other sides,
+ * and for ZM_PREC_DF64 with medium or high order; ZM_ERR_INVALID for ZM_PREC_FP32C combined
+ * with ZM_PREC_DF64. */
 int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double delta, int order,
               zm_ctx **out);
 

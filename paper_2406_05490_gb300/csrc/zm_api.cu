@@ -215,7 +215,7 @@ void zm_destroy(zm_ctx *c)
         c->y0 = c->ya = c->yb = c->u = c->phi = c->q = nullptr;
     }
     void *bufs[] = {c->y0, c->ya, c->yb, c->u, c->phi, c->q, c->nrm, c->src, c->part,
-                    c->fa, c->fb, c->tw1, c->tw2, c->err, c->flag};
+                    c->fa, c->fb, c->tw1, c->tw2, c->twl1, c->twl2, c->err, c->flag};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (prev >= 0) cudaSetDevice(prev);
@@ -248,10 +248,13 @@ int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double de
     if (fft && !mesh->periodic)
         return set_error(ZM_ERR_UNSUPPORTED,
                          "zm_create: low and medium order need a periodic mesh (periodic FFT solver)");
-    if (fft && (!pow2(mesh->n1) || !pow2(mesh->n2) || mesh->n1 > 4096 || mesh->n2 > 4096 ||
-                mesh->n1 < 8 || mesh->n2 < 8))
+    if (fft && df64 && (!pow2(mesh->n1) || !pow2(mesh->n2) || mesh->n1 > 4096 || mesh->n2 > 4096 ||
+                        mesh->n1 < 8 || mesh->n2 < 8))
         return set_error(ZM_ERR_UNSUPPORTED,
-                         "zm_create: low and medium order need power-of-two sides in [8, 4096]");
+                         "zm_create: double-word low order needs power-of-two sides in [8, 4096]");
+    if (fft && !df64 && (!fft_side_ok(mesh->n1) || !fft_side_ok(mesh->n2)))
+        return set_error(ZM_ERR_UNSUPPORTED,
+                         "zm_create: low and medium order need sides R 2^a <= 8192 (a >= 3, R odd <= 19)");
 
     zm_ctx *c = new (std::nothrow) zm_ctx();
     if (!c) return set_error(ZM_ERR_NOMEM, "zm_create: host allocation failed");

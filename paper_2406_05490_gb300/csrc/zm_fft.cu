@@ -14,6 +14,10 @@
 // Each CTA holds `rows` complete rows in shared memory and runs radix-2^2 butterflies there:
 // decimation in frequency (natural order in, bit-reversed out) for the forward transforms and
 // for pass C, decimation in time (bit-reversed in, natural out) for the inverse of pass B.
+// Sides L = R M with M = 2^a (a >= 3) and R odd (3 .. 19; 4864 = 19 x 256 is the paper's
+// low-order mesh, Sec. 5.1) add one radix-R stage: before the length-M transforms in decimation
+// in frequency, after them in decimation in time.  Frequency R k1 + k2 then sits at position
+// k2 M + bitrev(k1) of a row.
 #include <algorithm>
 
 #include "zm_internal.cuh"
@@ -136,10 +140,157 @@ __device__ void fft_dit(double2 *x, int rows, int L, const double2 *__restrict__
     }
 }
 
+// DFT of length R (odd) in registers, v[t] -> sum_t v[t] W_R^(t k), W_R = exp(sgn 2 pi i / R),
+// from the half table of W_L (W_R^e = W_L^(e M)).  Outputs k and R - k share the sums
+// A_k = v0 + sum_n (v_n + v_{R-n}) Re W^(nk) and B_k = sum_n (v_n - v_{R-n}) Im W^(nk):
+// X_k = A_k + i B_k, X_{R-k} = A_k - i B_k (W^(n(R-k)) is the conjugate of W^(nk)).
+template <int R>
+__device__ __forceinline__ void dft_small(double2 (&v)[R], const double2 *__restrict__ twl, int M, int half,
+                                          int sgn)
+{
+    constexpr int H = (R - 1) / 2;
+    double2 sm[H], df[H];
+    double2 x0 = v[0];
+#pragma unroll
+    for (int n = 1; n <= H; ++n) {
+        sm[n - 1] = cadd(v[n], v[R - n]);
+        df[n - 1] = csub(v[n], v[R - n]);
+        x0 = cadd(x0, sm[n - 1]);
+    }
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        double2 a = v[0], b = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int n = 1; n <= H; ++n) {
+            const double2 w = twiddle(twl, ((n * k) % R) * M, half, sgn);
+            a.x = fma(sm[n - 1].x, w.x, a.x);
+            a.y = fma(sm[n - 1].y, w.x, a.y);
+            b.x = fma(df[n - 1].x, w.y, b.x);
+            b.y = fma(df[n - 1].y, w.y, b.y);
+        }
+        v[k] = make_double2(a.x - b.y, a.y + b.x);      // a + i b
+        v[R - k] = make_double2(a.x + b.y, a.y - b.x);  // a - i b
+    }
+    v[0] = x0;
+}
+
+// Radix-R stage of decimation in frequency on `rows` rows of length L = R M in shared memory:
+// for each n1 < M the values x[n1 + M t] (t < R) become W_L^(n1 k) DFT_R(x)[k] at n1 + M k, so
+// that sub-row k (positions k M .. k M + M - 1) transforms, with length M, to outputs R k1 + k.
+template <int R>
+__device__ void radix_dif_r(double2 *x, int rows, int M, int lM, const double2 *__restrict__ twl, int sgn)
+{
+    const int L = R * M, half = L >> 1;
+    for (int b = threadIdx.x; b < rows * M; b += blockDim.x) {
+        const int row = b >> lM, n1 = b & (M - 1);
+        double2 *xr = x + (size_t)row * L + n1;
+        double2 v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = xr[t * M];
+        dft_small<R>(v, twl, M, half, sgn);
+        xr[0] = v[0];
+#pragma unroll
+        for (int k = 1; k < R; ++k) xr[k * M] = n1 ? cmul(v[k], twiddle(twl, n1 * k, half, sgn)) : v[k];
+    }
+    __syncthreads();
+}
+
+// The mirror stage of decimation in time: sub-row k holds, in natural order n1, the length-M
+// transform of the outputs R k1 + k; the values x[k M + n1] times W_L^(n1 k) go through DFT_R
+// over k, and output t lands at n1 + M t.
+template <int R>
+__device__ void radix_dit_r(double2 *x, int rows, int M, int lM, const double2 *__restrict__ twl, int sgn)
+{
+    const int L = R * M, half = L >> 1;
+    for (int b = threadIdx.x; b < rows * M; b += blockDim.x) {
+        const int row = b >> lM, n1 = b & (M - 1);
+        double2 *xr = x + (size_t)row * L + n1;
+        double2 v[R];
+        v[0] = xr[0];
+#pragma unroll
+        for (int k = 1; k < R; ++k) v[k] = n1 ? cmul(xr[k * M], twiddle(twl, n1 * k, half, sgn)) : xr[k * M];
+        dft_small<R>(v, twl, M, half, sgn);
+#pragma unroll
+        for (int t = 0; t < R; ++t) xr[t * M] = v[t];
+    }
+    __syncthreads();
+}
+
+#define ZM_FOR_RADICES(X) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(19)
+
+__device__ void radix_dif(double2 *x, int rows, int R, int M, int lM, const double2 *__restrict__ twl, int sgn)
+{
+    switch (R) {
+#define ZM_CASE(r) \
+    case r: radix_dif_r<r>(x, rows, M, lM, twl, sgn); break;
+        ZM_FOR_RADICES(ZM_CASE)
+#undef ZM_CASE
+    default: break;
+    }
+}
+
+__device__ void radix_dit(double2 *x, int rows, int R, int M, int lM, const double2 *__restrict__ twl, int sgn)
+{
+    switch (R) {
+#define ZM_CASE(r) \
+    case r: radix_dit_r<r>(x, rows, M, lM, twl, sgn); break;
+        ZM_FOR_RADICES(ZM_CASE)
+#undef ZM_CASE
+    default: break;
+    }
+}
+
+// One side of the transform: L = R M, M = 2^lM; tw = half table of W_M, twl = half table of W_L
+// (used only when R > 1).
+struct Side {
+    int L, R, M, lM;
+    const double2 *tw, *twl;
+};
+
+// Forward (sgn -1) or inverse (sgn +1) transform of `rows` rows by decimation in frequency.
+template <bool kMix>
+__device__ __forceinline__ void side_dif(double2 *x, int rows, const Side &s, int sgn)
+{
+    if (kMix) {
+        if (s.R > 1) radix_dif(x, rows, s.R, s.M, s.lM, s.twl, sgn);
+        fft_dif(x, rows * s.R, s.M, s.tw, sgn);
+    } else {
+        fft_dif(x, rows, s.L, s.tw, sgn);
+    }
+}
+
+template <bool kMix>
+__device__ __forceinline__ void side_dit(double2 *x, int rows, const Side &s, int sgn)
+{
+    if (kMix) {
+        fft_dit(x, rows * s.R, s.M, s.tw, sgn);
+        if (s.R > 1) radix_dit(x, rows, s.R, s.M, s.lM, s.twl, sgn);
+    } else {
+        fft_dit(x, rows, s.L, s.tw, sgn);
+    }
+}
+
+// Position in a row after decimation in frequency of the output with index f (natural order).
+template <bool kMix>
+__device__ __forceinline__ int dif_pos(int f, const Side &s)
+{
+    if (!kMix) return bitrev(f, s.lM);
+    const int k1 = f / s.R, k2 = f - k1 * s.R;
+    return k2 * s.M + bitrev(k1, s.lM);
+}
+
+// Output index f (natural order) held at position `pos` after decimation in frequency.
+template <bool kMix>
+__device__ __forceinline__ int dif_freq(int pos, const Side &s)
+{
+    if (!kMix) return bitrev(pos, s.lM);
+    return s.R * bitrev(pos & (s.M - 1), s.lM) + (pos >> s.lM);
+}
+
 // pass A: rows i of length n2 from w1 + i w2; forward; write out[j][i] (transposed).
+template <bool kMix>
 __global__ void __launch_bounds__(kFftTpb)
-    pass_a(int n1, int n2, int log2n2, int rows, const double *__restrict__ w,
-           const double2 *__restrict__ tw2, double2 *__restrict__ out)
+    pass_a(int n1, int n2, Side s2, int rows, const double *__restrict__ w, double2 *__restrict__ out)
 {
     extern __shared__ double2 sx[];
     const int i0 = blockIdx.x * rows;
@@ -150,28 +301,29 @@ __global__ void __launch_bounds__(kFftTpb)
         sx[e] = make_double2(w[p], w[N + p]);
     }
     __syncthreads();
-    fft_dif(sx, rows, n2, tw2, -1);
+    side_dif<kMix>(sx, rows, s2, -1);
     for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
         const int j = e / rows, r = e - j * rows;
-        out[(size_t)j * n1 + i0 + r] = sx[(size_t)r * n2 + bitrev(j, log2n2)];
+        out[(size_t)j * n1 + i0 + r] = sx[(size_t)r * n2 + dif_pos<kMix>(j, s2)];
     }
 }
 
 // pass B: rows j (length n1) of the transpose; forward; multiply; inverse; write out[i][j].
+template <bool kMix>
 __global__ void __launch_bounds__(kFftTpb)
-    pass_b(int n1, int n2, int log2n1, int rows, double invL1, double invL2,
-           const double2 *__restrict__ in, const double2 *__restrict__ tw1, double2 *__restrict__ out)
+    pass_b(int n1, int n2, Side s1, int rows, double invL1, double invL2, const double2 *__restrict__ in,
+           double2 *__restrict__ out)
 {
     extern __shared__ double2 sx[];
     const int j0 = blockIdx.x * rows;
     for (int e = threadIdx.x; e < rows * n1; e += blockDim.x) sx[e] = in[(size_t)j0 * n1 + e];
     __syncthreads();
-    fft_dif(sx, rows, n1, tw1, -1);
+    side_dif<kMix>(sx, rows, s1, -1);
     for (int e = threadIdx.x; e < rows * n1; e += blockDim.x) {
         const int r = e / n1, pos = e - r * n1;
-        const int i = bitrev(pos, log2n1), j = j0 + r;  // frequency indices
-        const int m1 = (i < n1 / 2) ? i : i - n1;
-        const int m2 = (j < n2 / 2) ? j : j - n2;
+        const int i = dif_freq<kMix>(pos, s1), j = j0 + r;  // frequency indices
+        const int m1 = (2 * i < n1) ? i : i - n1;
+        const int m2 = (2 * j < n2) ? j : j - n2;
         double2 v = make_double2(0.0, 0.0);
         if (!(m1 == 0 && m2 == 0) && 2 * i != n1 && 2 * j != n2) {
             // k_l / |k| with k_l = 2 pi m_l / L_l: the 2 pi cancels, t_l = m_l / L_l
@@ -183,7 +335,7 @@ __global__ void __launch_bounds__(kFftTpb)
         sx[e] = v;
     }
     __syncthreads();
-    fft_dit(sx, rows, n1, tw1, +1);
+    side_dit<kMix>(sx, rows, s1, +1);
     for (int e = threadIdx.x; e < rows * n1; e += blockDim.x) {
         const int i = e / rows, r = e - i * rows;
         out[(size_t)i * n2 + j0 + r] = sx[(size_t)r * n1 + i];
@@ -191,21 +343,22 @@ __global__ void __launch_bounds__(kFftTpb)
 }
 
 // pass C: rows i (length n2); inverse; s = Re / (n1 n2); u = -s/2 N; Phi = q + |u|^2 / 2.
+template <bool kMix>
 __global__ void __launch_bounds__(kFftTpb)
-    pass_c(int n1, int n2, int log2n2, int rows, double inv, const double2 *__restrict__ in,
-           const double2 *__restrict__ tw2, const double *__restrict__ nrm,
-           const double *__restrict__ q, double *__restrict__ u, double *__restrict__ phi)
+    pass_c(int n1, int n2, Side s2, int rows, double inv, const double2 *__restrict__ in,
+           const double *__restrict__ nrm, const double *__restrict__ q, double *__restrict__ u,
+           double *__restrict__ phi)
 {
     extern __shared__ double2 sx[];
     const int i0 = blockIdx.x * rows;
     const size_t N = (size_t)n1 * n2;
     for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) sx[e] = in[(size_t)i0 * n2 + e];
     __syncthreads();
-    fft_dif(sx, rows, n2, tw2, +1);
+    side_dif<kMix>(sx, rows, s2, +1);
     for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
         const int r = e / n2, j = e - r * n2;
         const size_t p = (size_t)(i0 + r) * n2 + j;
-        const double s = sx[(size_t)r * n2 + bitrev(j, log2n2)].x * inv;
+        const double s = sx[(size_t)r * n2 + dif_pos<kMix>(j, s2)].x * inv;
         const double ux = -0.5 * s * nrm[p], uy = -0.5 * s * nrm[N + p], uz = -0.5 * s * nrm[2 * N + p];
         u[p] = ux;
         u[N + p] = uy;
@@ -232,28 +385,86 @@ int ilog2(int n)
 
 int rows_for(int L) { return std::max(1, std::min(8, 4096 / L)); }
 
+// Largest row held in shared memory by one CTA: 8192 complex doubles (128 KiB).
+constexpr int kMaxSide = 8192;
+
+Side make_side(int L, const double2 *tw, const double2 *twl)
+{
+    Side s;
+    s.L = L;
+    s.M = L & -L;
+    s.R = L / s.M;
+    s.lM = ilog2(s.M);
+    s.tw = tw;
+    s.twl = twl;
+    return s;
+}
+
+template <bool kMix>
+int set_smem_limits()
+{
+    const int smax = kMaxSide * (int)sizeof(double2);
+    int rc = cuda_check(cudaFuncSetAttribute(pass_a<kMix>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax),
+                        "fft smem attribute");
+    if (!rc)
+        rc = cuda_check(cudaFuncSetAttribute(pass_b<kMix>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax),
+                        "fft smem attribute");
+    if (!rc)
+        rc = cuda_check(cudaFuncSetAttribute(pass_c<kMix>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax),
+                        "fft smem attribute");
+    return rc;
+}
+
+template <bool kMix>
+void launch_passes(zm_ctx *c, const double *w)
+{
+    const Geom &g = c->geom;
+    const Side s1 = make_side(g.n1, c->tw1, c->twl1), s2 = make_side(g.n2, c->tw2, c->twl2);
+    const int ra = rows_for(g.n2), rb = rows_for(g.n1);
+    pass_a<kMix><<<g.n1 / ra, kFftTpb, ra * g.n2 * sizeof(double2), c->stream>>>(g.n1, g.n2, s2, ra, w, c->fa);
+    pass_b<kMix><<<g.n2 / rb, kFftTpb, rb * g.n1 * sizeof(double2), c->stream>>>(
+        g.n1, g.n2, s1, rb, 1.0 / g.L1, 1.0 / g.L2, c->fa, c->fb);
+    pass_c<kMix><<<g.n1 / ra, kFftTpb, ra * g.n2 * sizeof(double2), c->stream>>>(
+        g.n1, g.n2, s2, ra, 1.0 / ((double)g.n1 * (double)g.n2), c->fb, c->nrm, c->q, c->u, c->phi);
+}
+
 }  // namespace
+
+bool fft_side_ok(int L)
+{
+    if (L < 8 || L > kMaxSide) return false;
+    const int M = L & -L, R = L / M;
+    if (M < 8) return false;
+    switch (R) {
+    case 1:
+#define ZM_CASE(r) case r:
+        ZM_FOR_RADICES(ZM_CASE)
+#undef ZM_CASE
+        return true;
+    default: return false;
+    }
+}
 
 int fft_setup(zm_ctx *c)
 {
     const Geom &g = c->geom;
     const size_t N = g.N;
+    const Side s1 = make_side(g.n1, nullptr, nullptr), s2 = make_side(g.n2, nullptr, nullptr);
     if (cudaMalloc(&c->fa, N * sizeof(double2)) != cudaSuccess ||
         cudaMalloc(&c->fb, N * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc(&c->tw1, (g.n1 / 2) * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc(&c->tw2, (g.n2 / 2) * sizeof(double2)) != cudaSuccess) {
+        cudaMalloc(&c->tw1, (s1.M / 2) * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&c->tw2, (s2.M / 2) * sizeof(double2)) != cudaSuccess ||
+        (s1.R > 1 && cudaMalloc(&c->twl1, (g.n1 / 2) * sizeof(double2)) != cudaSuccess) ||
+        (s2.R > 1 && cudaMalloc(&c->twl2, (g.n2 / 2) * sizeof(double2)) != cudaSuccess)) {
         cudaGetLastError();
         return set_error(ZM_ERR_NOMEM, "fft_setup: device allocation failed");
     }
-    twiddle_kernel<<<(g.n1 / 2 + 255) / 256, 256>>>(g.n1, c->tw1);
-    twiddle_kernel<<<(g.n2 / 2 + 255) / 256, 256>>>(g.n2, c->tw2);
-    const int smax = 8 * 4096 * (int)sizeof(double2) / 8;  // rows * L * 16 <= 64 KiB
-    int rc = cuda_check(cudaFuncSetAttribute(pass_a, cudaFuncAttributeMaxDynamicSharedMemorySize, smax),
-                        "fft smem attribute");
-    if (!rc) rc = cuda_check(cudaFuncSetAttribute(pass_b, cudaFuncAttributeMaxDynamicSharedMemorySize, smax),
-                             "fft smem attribute");
-    if (!rc) rc = cuda_check(cudaFuncSetAttribute(pass_c, cudaFuncAttributeMaxDynamicSharedMemorySize, smax),
-                             "fft smem attribute");
+    twiddle_kernel<<<(s1.M / 2 + 255) / 256, 256>>>(s1.M, c->tw1);
+    twiddle_kernel<<<(s2.M / 2 + 255) / 256, 256>>>(s2.M, c->tw2);
+    if (c->twl1) twiddle_kernel<<<(g.n1 / 2 + 255) / 256, 256>>>(g.n1, c->twl1);
+    if (c->twl2) twiddle_kernel<<<(g.n2 / 2 + 255) / 256, 256>>>(g.n2, c->twl2);
+    int rc = set_smem_limits<false>();
+    if (!rc) rc = set_smem_limits<true>();
     if (!rc) rc = cuda_check(cudaGetLastError(), "twiddle kernel");
     return rc;
 }
@@ -263,17 +474,17 @@ int launch_riesz(zm_ctx *c, const double *y)
     if (!y || !c->fa || !c->fb || !c->tw1 || !c->tw2 || !c->nrm || !c->q || !c->u || !c->phi)
         return set_error(ZM_ERR_INVALID, "Riesz pass: missing buffer");
     const Geom &g = c->geom;
-    const int l1 = ilog2(g.n1), l2 = ilog2(g.n2);
-    const int ra = rows_for(g.n2), rb = rows_for(g.n1);
+    const bool pow1 = (g.n1 & (g.n1 - 1)) == 0, pow2 = (g.n2 & (g.n2 - 1)) == 0;
+    if ((!pow1 && !c->twl1) || (!pow2 && !c->twl2))
+        return set_error(ZM_ERR_INVALID, "Riesz pass: missing twiddle table");
+    const bool mix = !(pow1 && pow2);
     const double *w = y + 3 * (size_t)g.N;
     cudaEvent_t ev = nullptr;
     prof_begin(c, ZM_K_FFT, &ev);
-    pass_a<<<g.n1 / ra, kFftTpb, ra * g.n2 * sizeof(double2), c->stream>>>(g.n1, g.n2, l2, ra, w,
-                                                                            c->tw2, c->fa);
-    pass_b<<<g.n2 / rb, kFftTpb, rb * g.n1 * sizeof(double2), c->stream>>>(
-        g.n1, g.n2, l1, rb, 1.0 / g.L1, 1.0 / g.L2, c->fa, c->tw1, c->fb);
-    pass_c<<<g.n1 / ra, kFftTpb, ra * g.n2 * sizeof(double2), c->stream>>>(
-        g.n1, g.n2, l2, ra, 1.0 / ((double)g.n1 * (double)g.n2), c->fb, c->tw2, c->nrm, c->q, c->u, c->phi);
+    if (mix)
+        launch_passes<true>(c, w);
+    else
+        launch_passes<false>(c, w);
     prof_end(c, ZM_K_FFT, ev);
     c->prof.acc.launches[ZM_K_FFT] += 2;  // three kernels per Riesz evaluation
     return cuda_check(cudaGetLastError(), "Riesz FFT launch");

@@ -134,8 +134,9 @@ struct zm_ctx {
     float4 *tinfo;    // FP32C per-tile bounding sphere: centre, radius
     zm::Br32Plan plan32;
 
-    // low order: FFT workspace (complex doubles) and twiddles
-    double2 *fa, *fb, *tw1, *tw2;
+    // low order: FFT workspace (complex doubles) and twiddles: tw1, tw2 for the power-of-two
+    // factor M of each side, twl1, twl2 for the whole side L = R M when R > 1 (else null)
+    double2 *fa, *fb, *tw1, *tw2, *twl1, *twl2;
 
     int *err;   // device status word (zm::kErr*)
     int *flag;  // device scratch flag (finite check)
@@ -190,6 +191,8 @@ int launch_br32_batch(const Inst *d_insts, int ninst, long long nitems, int ctas
 void init_far_records(float *far_rec, int ntiles, float d2, cudaStream_t s);
 
 // ---- low order (zm_fft.cu) ---------------------------------------------------------------------
+// Sides the FP64 FFT takes: L = R 2^a with a >= 3, R odd in 1 .. 19, L <= 8192.
+bool fft_side_ok(int L);
 int fft_setup(zm_ctx *c);
 int launch_riesz(zm_ctx *c, const double *y);
 

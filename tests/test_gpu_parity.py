@@ -83,7 +83,10 @@ def test_single_mode_steps_config1(zm, fp32c):
     assert ez <= tol and ew <= tol and dz <= (1e-5 if fp32c else 1e-10)
 
 
-@pytest.mark.parametrize("n1,n2", [(8, 8), (64, 32), (128, 128), (16, 256)])
+@pytest.mark.parametrize("n1,n2", [(8, 8), (64, 32), (128, 128), (16, 256),
+                                   # sides R 2^a: every odd factor R = 3 .. 19 once, a = 3 .. 6
+                                   (24, 40), (56, 72), (88, 104), (120, 136), (152, 16), (96, 320),
+                                   (608, 152)])
 def test_low_order_parity(zm, n1, n2):
     z, w = inputs.random_state(n1, n2, seed=n1 + n2)
     m = oracle.Mesh(n1, n2, periodic=True)
@@ -97,7 +100,7 @@ def test_low_order_parity(zm, n1, n2):
 
 
 @pytest.mark.parametrize("fp32c", [False, True])
-@pytest.mark.parametrize("n1,n2", [(16, 16), (64, 32)])
+@pytest.mark.parametrize("n1,n2", [(16, 16), (64, 32), (24, 40)])
 def test_medium_order_parity(zm, n1, n2, fp32c):
     """Medium order: dz/dt from the Birkhoff-Rott sum, Phi from the FFT velocity."""
     tol = TOL32 if fp32c else TOL64
@@ -221,6 +224,37 @@ def test_low_order_2048_full(zm):
     assert eu <= TOL64 and ew <= TOL64
 
 
+def test_low_order_4864_full(zm):
+    """The paper's single-GPU low-order mesh, 4864^2 = 19 x 256 per side (23.7 M points): all of
+    u and dw/dt against the oracle, and three RK3 steps against the oracle's steps on a
+    sample of rows."""
+    n = 4864
+    z, _ = inputs.multi_mode(n, n_modes=8, seed=9, amp=0.02)
+    _, w = inputs.random_state(n, seed=15)
+    m = oracle.Mesh(n, periodic=True)
+    u_ref, wd_ref = oracle.derivative(m, z, w, 0.7, 1.0, 0.0, 0.0, order=oracle.ORDER_LOW)
+    model = zm.ZModel(n, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW)
+    u, wd = model.velocity(z, w)
+    model.close()
+    eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+    print(f"low order 4864^2: rel L2 u={eu:.3e} wdot={ew:.3e}")
+    assert eu <= TOL64 and ew <= TOL64
+
+
+def test_low_order_steps_mixed_sides(zm):
+    n1, n2 = 96, 152
+    z0, w0 = inputs.random_state(n1, n2, seed=31)
+    m = oracle.Mesh(n1, n2, periodic=True)
+    zr, wr = oracle.run(m, z0, w0, 0.7, 1.0, 0.01, 0.0, 1e-3, 4, order=oracle.ORDER_LOW)
+    model = zm.ZModel(n1, n2, periodic=True, atwood=0.7, g=1.0, mu=0.01, order=zm.ZM_ORDER_LOW)
+    model.set_state(z0, w0)
+    model.step(1e-3, 4)
+    z1, w1 = model.get_state()
+    model.close()
+    print(f"low order steps 96x152: rel L2 z={rel(z1, zr):.3e} w={rel(w1, wr):.3e}")
+    assert rel(z1, zr) <= TOL64 and rel(w1, wr) <= TOL64
+
+
 def test_deterministic_and_device_pointers(zm):
     import torch
     n = 48
@@ -249,9 +283,11 @@ def test_invalid_arguments(zm):
     with pytest.raises(zm.ZMError) as e:
         zm.zm_create(32, 32, periodic=False, order=zm.ZM_ORDER_LOW)
     assert e.value.code == zm.ZM_ERR_UNSUPPORTED
-    with pytest.raises(zm.ZMError) as e:
-        zm.zm_create(48, 48, periodic=True, order=zm.ZM_ORDER_LOW)
-    assert e.value.code == zm.ZM_ERR_UNSUPPORTED
+    # FFT sides R 2^a need a >= 3 and R <= 19; double words take powers of two only
+    for n1, n2, prec in ((12, 16, 0), (168, 64, 0), (64, 44, 0), (48, 48, zm.ZM_PREC_DF64)):
+        with pytest.raises(zm.ZMError) as e:
+            zm.zm_create(n1, n2, periodic=True, order=zm.ZM_ORDER_LOW | prec)
+        assert e.value.code == zm.ZM_ERR_UNSUPPORTED
     with pytest.raises(zm.ZMError) as e:
         zm.zm_create(32, 32, periodic=False, order=zm.ZM_ORDER_MEDIUM)
     assert e.value.code == zm.ZM_ERR_UNSUPPORTED

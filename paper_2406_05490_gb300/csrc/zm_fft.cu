@@ -383,7 +383,14 @@ int ilog2(int n)
     return l;
 }
 
-int rows_for(int L) { return std::max(1, std::min(8, 4096 / L)); }
+// Rows per CTA: a power of two (it must divide the other side, which has a factor 2^3), at most
+// 8 and at most 4096 / L.
+int rows_for(int L)
+{
+    int r = 8;
+    while (r > 1 && r * L > 4096) r >>= 1;
+    return r;
+}
 
 // Largest row held in shared memory by one CTA: 8192 complex doubles (128 KiB).
 constexpr int kMaxSide = 8192;
@@ -416,16 +423,18 @@ int set_smem_limits()
 }
 
 template <bool kMix>
-void launch_passes(zm_ctx *c, const double *w)
+int launch_passes(zm_ctx *c, const double *w)
 {
     const Geom &g = c->geom;
     const Side s1 = make_side(g.n1, c->tw1, c->twl1), s2 = make_side(g.n2, c->tw2, c->twl2);
     const int ra = rows_for(g.n2), rb = rows_for(g.n1);
+    if (g.n1 % ra || g.n2 % rb) return set_error(ZM_ERR_INVALID, "Riesz pass: rows per CTA do not divide the side");
     pass_a<kMix><<<g.n1 / ra, kFftTpb, ra * g.n2 * sizeof(double2), c->stream>>>(g.n1, g.n2, s2, ra, w, c->fa);
     pass_b<kMix><<<g.n2 / rb, kFftTpb, rb * g.n1 * sizeof(double2), c->stream>>>(
         g.n1, g.n2, s1, rb, 1.0 / g.L1, 1.0 / g.L2, c->fa, c->fb);
     pass_c<kMix><<<g.n1 / ra, kFftTpb, ra * g.n2 * sizeof(double2), c->stream>>>(
         g.n1, g.n2, s2, ra, 1.0 / ((double)g.n1 * (double)g.n2), c->fb, c->nrm, c->q, c->u, c->phi);
+    return ZM_OK;
 }
 
 }  // namespace
@@ -481,11 +490,9 @@ int launch_riesz(zm_ctx *c, const double *y)
     const double *w = y + 3 * (size_t)g.N;
     cudaEvent_t ev = nullptr;
     prof_begin(c, ZM_K_FFT, &ev);
-    if (mix)
-        launch_passes<true>(c, w);
-    else
-        launch_passes<false>(c, w);
+    const int rc = mix ? launch_passes<true>(c, w) : launch_passes<false>(c, w);
     prof_end(c, ZM_K_FFT, ev);
+    if (rc) return rc;
     c->prof.acc.launches[ZM_K_FFT] += 2;  // three kernels per Riesz evaluation
     return cuda_check(cudaGetLastError(), "Riesz FFT launch");
 }

@@ -225,15 +225,23 @@ def test_low_order_2048_full(zm):
 
 
 def test_low_order_4864_full(zm):
-    """The paper's single-GPU low-order mesh, 4864^2 = 19 x 256 per side (23.7 M points): all of
-    u and dw/dt against the oracle, and three RK3 steps against the oracle's steps on a
-    sample of rows."""
-    n = 4864
-    z, _ = inputs.multi_mode(n, n_modes=8, seed=9, amp=0.02)
+    """The paper's single-GPU low-order mesh and domain (Sec. 5.1): 4864^2 nodes (19 x 256 per
+    side, 23.7 M points) over (-19, 19)^2, so dx = 38 / 4864 = 2^-7 and the mesh coordinates are
+    exact.  All of u and dw/dt against the oracle.
+
+    (On the unit square dx = 1/4864 is inexact: the coordinates z1 = alpha1 then carry roundings
+    of about eps |z1|, and the difference stencil turns the roundings of its own sums into
+    tangent errors of about eps |z1| / dx, in the oracle and the kernels alike but in different
+    operation orders; there the two agree to 7e-14 on u and 1.2e-12 on dw/dt.)"""
+    n, L = 4864, 38.0
+    zu, _ = inputs.multi_mode(n, n_modes=8, seed=9, amp=0.02)
+    a, b = inputs.mesh_coords(n, n, L, L)
+    z = np.stack([a, b, L * zu[2]])
+    del zu
     _, w = inputs.random_state(n, seed=15)
-    m = oracle.Mesh(n, periodic=True)
+    m = oracle.Mesh(n, n, L1=L, L2=L, periodic=True)
     u_ref, wd_ref = oracle.derivative(m, z, w, 0.7, 1.0, 0.0, 0.0, order=oracle.ORDER_LOW)
-    model = zm.ZModel(n, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW)
+    model = zm.ZModel(n, L1=L, L2=L, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW)
     u, wd = model.velocity(z, w)
     model.close()
     eu, ew = rel(u, u_ref), rel(wd, wd_ref)

@@ -648,6 +648,7 @@ def run_gb300(args):
         extras["low_order_4096_df64"] = bench_low_order(zm, torch, inputs, flush, 4096, 5, 2, True)
         # the paper's single-GPU low-order mesh: 4864^2 = (19 x 256)^2, FP64 (radix-19 stage)
         extras["low_order_4864"] = bench_low_order(zm, torch, inputs, flush, 4864, 3, 1, False)
+        extras["low_order_4864_df64"] = bench_low_order(zm, torch, inputs, flush, 4864, 5, 2, True)
         # 32^2 single-mode FP64 (launch bound)
         zs, wsn = inputs.single_mode(32)
         ms_ = zm.ZModel(32, periodic=False, atwood=0.5, g=1.0, delta=0.1 / 32)

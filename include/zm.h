@@ -88,7 +88,7 @@ typedef struct zm_ctx zm_ctx;
  * size (high order); mu >= 0 the artificial viscosity; `order` is ZM_ORDER_* | ZM_PREC_*.
  * Low and medium order (periodic FFT solver, Sec. 2 and 3.1) take sides L = R 2^a with a >= 3,
  * R odd in 1 .. 19 and L <= 8192 (the paper's 4864 = 19 x 2^8 among them); ZM_PREC_DF64 takes
- * powers of two from 8 to 4096.
+ * the same sides except powers of two above 4096.
  * Returns ZM_ERR_UNSUPPORTED for low or medium order on a free-edge mesh or on other sides,
  * and for ZM_PREC_DF64 with medium or high order; ZM_ERR_INVALID for ZM_PREC_FP32C combined
  * with ZM_PREC_DF64. */

@@ -197,7 +197,6 @@ const char *zm_error_string(int code)
 
 const char *zm_last_error(void) { return g_last_error.c_str(); }
 
-static bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 void zm_destroy(zm_ctx *c)
 {
@@ -248,10 +247,9 @@ int zm_create(const zm_mesh *mesh, double atwood, double g, double mu, double de
     if (fft && !mesh->periodic)
         return set_error(ZM_ERR_UNSUPPORTED,
                          "zm_create: low and medium order need a periodic mesh (periodic FFT solver)");
-    if (fft && df64 && (!pow2(mesh->n1) || !pow2(mesh->n2) || mesh->n1 > 4096 || mesh->n2 > 4096 ||
-                        mesh->n1 < 8 || mesh->n2 < 8))
+    if (fft && df64 && (!df_side_ok(mesh->n1) || !df_side_ok(mesh->n2)))
         return set_error(ZM_ERR_UNSUPPORTED,
-                         "zm_create: double-word low order needs power-of-two sides in [8, 4096]");
+                         "zm_create: double-word low order needs sides 2^a <= 4096 or R 2^a <= 8192 (3 <= a <= 12, R odd <= 19)");
     if (fft && !df64 && (!fft_side_ok(mesh->n1) || !fft_side_ok(mesh->n2)))
         return set_error(ZM_ERR_UNSUPPORTED,
                          "zm_create: low and medium order need sides R 2^a <= 8192 (a >= 3, R odd <= 19)");

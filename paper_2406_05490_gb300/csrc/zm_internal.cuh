@@ -193,6 +193,9 @@ void init_far_records(float *far_rec, int ntiles, float d2, cudaStream_t s);
 // ---- low order (zm_fft.cu) ---------------------------------------------------------------------
 // Sides the FP64 FFT takes: L = R 2^a with a >= 3, R odd in 1 .. 19, L <= 8192.
 bool fft_side_ok(int L);
+// Sides the double-word FFT takes: powers of two 8 .. 4096, or R 2^a with a in 3 .. 12, R odd in
+// 3 .. 19, L <= 8192.
+bool df_side_ok(int L);
 int fft_setup(zm_ctx *c);
 int launch_riesz(zm_ctx *c, const double *y);
 

@@ -45,7 +45,11 @@ def zm():
 
 
 @pytest.mark.parametrize("n1,n2,mu", [(8, 8, 0.0), (64, 32, 0.0), (128, 128, 0.01), (16, 256, 0.0),
-                                      (256, 64, 0.003), (32, 8, 0.0)])
+                                      (256, 64, 0.003), (32, 8, 0.0),
+                                      # sides R 2^A: every odd factor R = 3 .. 19 once, A = 3 .. 11
+                                      (24, 40, 0.0), (56, 72, 0.01), (88, 104, 0.0), (120, 136, 0.0),
+                                      (152, 16, 0.0), (96, 320, 0.003), (608, 152, 0.0), (6144, 8, 0.0),
+                                      (8, 6144, 0.0)])
 def test_df64_velocity_parity(zm, n1, n2, mu):
     z, w = inputs.random_state(n1, n2, seed=n1 + 2 * n2)
     m = oracle.Mesh(n1, n2, periodic=True)
@@ -178,7 +182,46 @@ def test_df64_graph_replay_equals_plain_launches(zm):
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
+def test_df64_4864_full(zm):
+    """The paper's single-GPU low-order mesh and domain (Sec. 5.1): 4864^2 nodes over (-19, 19)^2
+    (dx = 2^-7), all of u and dw/dt against the oracle within the double-word bounds."""
+    n, L = 4864, 38.0
+    zu, _ = inputs.multi_mode(n, n_modes=8, seed=9, amp=0.02)
+    a, b = inputs.mesh_coords(n, n, L, L)
+    z = np.stack([a, b, L * zu[2]])
+    del zu
+    _, w = inputs.random_state(n, seed=15)
+    m = oracle.Mesh(n, n, L1=L, L2=L, periodic=True)
+    u_ref, wd_ref = oracle.derivative(m, z, w, 0.7, 1.0, 0.0, 0.0, order=oracle.ORDER_LOW)
+    model = zm.ZModel(n, L1=L, L2=L, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW, df64=True)
+    u, wd = model.velocity(z, w)
+    model.close()
+    eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+    tw = wdot_tol(n, 0.0, w, wd_ref)
+    print(f"df64 low order 4864^2: rel L2 u={eu:.3e} wdot={ew:.3e} (bound {tw:.1e})")
+    assert eu <= TOL and ew <= tw
+
+
+def test_df64_steps_mixed_sides(zm):
+    n1, n2 = 96, 152
+    z0, w0 = inputs.random_state(n1, n2, seed=33)
+    m = oracle.Mesh(n1, n2, periodic=True)
+    zr, wr = oracle.run(m, z0, w0, 0.7, 1.0, 0.01, 0.0, 1e-3, 4, order=oracle.ORDER_LOW)
+    model = zm.ZModel(n1, n2, periodic=True, atwood=0.7, g=1.0, mu=0.01, order=zm.ZM_ORDER_LOW, df64=True)
+    model.set_state(z0, w0)
+    model.step(1e-3, 4)
+    z1, w1 = model.get_state()
+    model.close()
+    ez, ew, dz = rel(z1, zr), rel(w1, wr), rel(z1 - z0, zr - z0)
+    print(f"df64 4 steps 96x152: rel L2 z={ez:.3e} w={ew:.3e} (z - z0)={dz:.3e}")
+    assert ez <= TOL and ew <= TOL and dz <= 1e-10
+
+
 def test_df64_flag_rules(zm):
+    for n1, n2 in ((12, 16), (168, 64), (64, 44), (8192, 8)):
+        with pytest.raises(zm.ZMError) as e:
+            zm.zm_create(n1, n2, periodic=True, order=zm.ZM_ORDER_LOW | zm.ZM_PREC_DF64)
+        assert e.value.code == zm.ZM_ERR_UNSUPPORTED
     with pytest.raises(zm.ZMError) as e:
         zm.zm_create(32, 32, periodic=True, delta=0.01, order=zm.ZM_ORDER_HIGH | zm.ZM_PREC_DF64)
     assert e.value.code == zm.ZM_ERR_UNSUPPORTED

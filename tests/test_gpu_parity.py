@@ -291,8 +291,8 @@ def test_invalid_arguments(zm):
     with pytest.raises(zm.ZMError) as e:
         zm.zm_create(32, 32, periodic=False, order=zm.ZM_ORDER_LOW)
     assert e.value.code == zm.ZM_ERR_UNSUPPORTED
-    # FFT sides R 2^a need a >= 3 and R <= 19; double words take powers of two only
-    for n1, n2, prec in ((12, 16, 0), (168, 64, 0), (64, 44, 0), (48, 48, zm.ZM_PREC_DF64)):
+    # FFT sides R 2^a need a >= 3 and R <= 19 (double words: powers of two up to 4096 only)
+    for n1, n2, prec in ((12, 16, 0), (168, 64, 0), (64, 44, 0), (8192, 8, zm.ZM_PREC_DF64)):
         with pytest.raises(zm.ZMError) as e:
             zm.zm_create(n1, n2, periodic=True, order=zm.ZM_ORDER_LOW | prec)
         assert e.value.code == zm.ZM_ERR_UNSUPPORTED

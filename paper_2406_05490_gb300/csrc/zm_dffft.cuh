@@ -350,7 +350,7 @@ int df_mix_pass_a(int A, int n1, int R, int lr, size_t smem, cudaStream_t s, con
                   const ulonglong2 *tw2, const ulonglong2 *twl2, ulonglong2 *out);
 int df_mix_pass_b(int A, int n2, int R, int lr, size_t smem, cudaStream_t s, double invL1, double invL2,
                   const ulonglong2 *in, const ulonglong2 *tw1, const ulonglong2 *twl1, ulonglong2 *out);
-int df_mix_pass_c(int A, int n1, int R, int lr, size_t smem, cudaStream_t s, float scale, const ulonglong2 *in,
+int df_mix_pass_c(int A, int n1, int R, int lr, size_t smem, cudaStream_t s, double scale, const ulonglong2 *in,
                   const ulonglong2 *tw2, const ulonglong2 *twl2, const float2 *nrm, const float2 *q, float2 *u,
                   float2 *phi);
 // Radices the double-word passes take.

@@ -48,8 +48,8 @@ __device__ __forceinline__ int wrap(int a, int d, int n)
     return b < 0 ? b + n : (b >= n ? b - n : b);
 }
 
-// Mesh indices of node p; kP2: n2 is a power of two (shift and mask), else a multiply-shift
-// division exact for p < 2^26 and n2 <= 2^13.
+// Mesh indices of node p; kP2: both sides are powers of two (shift and mask), else a
+// multiply-shift division exact for p < 2^26 and n2 <= 2^13.
 template <bool kP2>
 __device__ __forceinline__ void node_ij(int p, const DfGeo &g, int &i, int &j)
 {
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(threads_for(L), minb_for(L))
 // pass C: rows i (length n2 = 2^L); inverse; s = Re / (n1 n2); u = -s/2 N; Phi = q + |u|^2 / 2.
 template <int L>
 __global__ void __launch_bounds__(threads_for(L), minb_for(L))
-    pass_c_df(int n1, int lr, float scale, const ulonglong2 *__restrict__ in,
+    pass_c_df(int n1, int lr, Dc scale, const ulonglong2 *__restrict__ in,
               const ulonglong2 *__restrict__ tw2, const float2 *__restrict__ nrm,
               const float2 *__restrict__ q, float2 *__restrict__ u, float2 *__restrict__ phi)
 {
@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(threads_for(L), minb_for(L))
     for (int e = threadIdx.x; e < (rows << L); e += blockDim.x) {
         const int r = e >> L, j = e & ((1 << L) - 1);
         const size_t p = o + e;
-        const df s = scale2(c2_re(ld2(sx[phys((r << L) + bitrev(j, L))])), scale);  // scale = -1/(2 n1 n2)
+        // scale = -1/(2 n1 n2) as a double word (a power of two only when both sides are)
+        const df s = mul(c2_re(ld2(sx[phys((r << L) + bitrev(j, L))])), dc(scale));
         const df ux = mul(s, ldf(nrm, p)), uy = mul(s, ldf(nrm, N + p)), uz = mul(s, ldf(nrm, 2 * N + p));
         u[p] = to_f2(ux);
         u[N + p] = to_f2(uy);
@@ -384,7 +385,7 @@ struct FftLaunch {
         pass_b_df<L><<<n2 >> lr, threads_for(L), smem, s>>>(n2, lr, invL1, invL2, in, tw1, out);
         return cuda_check(cudaGetLastError(), "double-word FFT pass B launch");
     }
-    static int c(int n1, int lr, size_t smem, cudaStream_t s, float scale, const ulonglong2 *in,
+    static int c(int n1, int lr, size_t smem, cudaStream_t s, Dc scale, const ulonglong2 *in,
                  const ulonglong2 *tw2, const float2 *nrm, const float2 *q, float2 *u, float2 *phi)
     {
         int rc = smem_attr((const void *)pass_c_df<L>, smem);
@@ -455,7 +456,7 @@ int df_derivative(zm_ctx *c, const double *y)
     cudaEvent_t ev = nullptr;
     prof_begin(c, ZM_K_GEOMETRY, &ev);
     const int grid = (G.N + kTpb - 1) / kTpb;
-    if (pow2_side(G.n2))
+    if (pow2_side(G.n1) && pow2_side(G.n2))  // shift-and-mask indexing needs both sides
         geometry_df<true><<<grid, kTpb, 0, c->stream>>>(g, F2(y), F2(c->q), F2(c->nrm));
     else
         geometry_df<false><<<grid, kTpb, 0, c->stream>>>(g, F2(y), F2(c->q), F2(c->nrm));
@@ -472,7 +473,7 @@ int df_derivative(zm_ctx *c, const double *y)
         return set_error(ZM_ERR_INVALID, "double-word derivative: rows per CTA do not divide the side");
     const size_t sa = (size_t)phys_host(G.n2 << ra) * sizeof(ulonglong2);
     const size_t sb = (size_t)phys_host(G.n1 << rb) * sizeof(ulonglong2);
-    const float scale = (float)(-0.5 / ((double)G.n1 * (double)G.n2));
+    const double scale = -0.5 / ((double)G.n1 * (double)G.n2);
     const float2 *w = F2(y) + 3 * (size_t)G.N;
     const Dc iL1 = split(1.0 / G.L1), iL2 = split(1.0 / G.L2);
     prof_begin(c, ZM_K_FFT, &ev);
@@ -491,7 +492,7 @@ int df_derivative(zm_ctx *c, const double *y)
         constexpr int A = decltype(lc)::value;
         return s2.R > 1 ? df_mix_pass_c(A, G.n1, s2.R, ra, sa, c->stream, scale, U2(c->fb), U2(c->tw2),
                                         U2(c->twl2), F2(c->nrm), F2(c->q), F2(c->u), F2(c->phi))
-                        : FftLaunch<A>::c(G.n1, ra, sa, c->stream, scale, U2(c->fb), U2(c->tw2), F2(c->nrm),
+                        : FftLaunch<A>::c(G.n1, ra, sa, c->stream, split(scale), U2(c->fb), U2(c->tw2), F2(c->nrm),
                                           F2(c->q), F2(c->u), F2(c->phi));
     });
     prof_end(c, ZM_K_FFT, ev);
@@ -509,7 +510,7 @@ int df_vorticity(zm_ctx *c, const double *y, double *wdot_out, const double *y0,
     const int grid = (c->geom.N + kTpb - 1) / kTpb;
     cudaEvent_t ev = nullptr;
     prof_begin(c, ZM_K_VORT, &ev);
-    const bool visc = (c->mu != 0.0), p2 = pow2_side(c->geom.n2);
+    const bool visc = (c->mu != 0.0), p2 = pow2_side(c->geom.n1) && pow2_side(c->geom.n2);
 #define ZM_VDF(V, M, P)                                                                                      \
     vorticity_df<V, M, P><<<grid, kTpb, 0, c->stream>>>(g, F2(c->phi), F2(y), F2(c->u), split(dt), split(ca), \
                                                         split(cb), F2(y0), F2(yout), F2(wdot_out))

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kMixTpb, 1)
 // pass C on rows of length n2 = R 2^A.
 template <int A>
 __global__ void __launch_bounds__(kMixTpb, 1)
-    pass_c_dfm(int n1, int R, int lr, float scale, const ulonglong2 *__restrict__ in,
+    pass_c_dfm(int n1, int R, int lr, Dc scale, const ulonglong2 *__restrict__ in,
                const ulonglong2 *__restrict__ tw2, const ulonglong2 *__restrict__ twl2, const float2 *__restrict__ nrm,
                const float2 *__restrict__ q, float2 *__restrict__ u, float2 *__restrict__ phi)
 {
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kMixTpb, 1)
     for (int e = threadIdx.x; e < rows * L; e += blockDim.x) {
         const int r = e / L, j = e - r * L;
         const size_t p = o + e;
-        const df s = scale2(c2_re(ld2(sx[phys(r * L + mix_pos<A>(j, R))])), scale);  // scale = -1/(2 n1 n2)
+        const df s = mul(c2_re(ld2(sx[phys(r * L + mix_pos<A>(j, R))])), dc(scale));  // -1/(2 n1 n2)
         const df ux = mul(s, ldf(nrm, p)), uy = mul(s, ldf(nrm, N + p)), uz = mul(s, ldf(nrm, 2 * N + p));
         u[p] = to_f2(ux);
         u[N + p] = to_f2(uy);
@@ -235,7 +235,7 @@ struct FftLaunchMix {
         pass_b_dfm<A><<<n2 >> lr, kMixTpb, smem, s>>>(n2, R, lr, invL1, invL2, in, tw1, twl1, out);
         return cuda_check(cudaGetLastError(), "double-word FFT pass B launch");
     }
-    static int c(int n1, int R, int lr, size_t smem, cudaStream_t s, float scale, const ulonglong2 *in,
+    static int c(int n1, int R, int lr, size_t smem, cudaStream_t s, Dc scale, const ulonglong2 *in,
                  const ulonglong2 *tw2, const ulonglong2 *twl2, const float2 *nrm, const float2 *q, float2 *u,
                  float2 *phi)
     {
@@ -262,12 +262,12 @@ int df_mix_pass_b(int A, int n2, int R, int lr, size_t smem, cudaStream_t s, dou
     });
 }
 
-int df_mix_pass_c(int A, int n1, int R, int lr, size_t smem, cudaStream_t s, float scale, const ulonglong2 *in,
+int df_mix_pass_c(int A, int n1, int R, int lr, size_t smem, cudaStream_t s, double scale, const ulonglong2 *in,
                   const ulonglong2 *tw2, const ulonglong2 *twl2, const float2 *nrm, const float2 *q, float2 *u,
                   float2 *phi)
 {
     return with_log2(A, [&](auto lc) {
-        return FftLaunchMix<decltype(lc)::value>::c(n1, R, lr, smem, s, scale, in, tw2, twl2, nrm, q, u, phi);
+        return FftLaunchMix<decltype(lc)::value>::c(n1, R, lr, smem, s, split(scale), in, tw2, twl2, nrm, q, u, phi);
     });
 }
 

@@ -4,12 +4,14 @@ FP32 pairs, ~48-bit significand) against the CPU oracle, through the C ABI.
 Tolerances (relative L2 per field), derived from the arithmetic; u^2 = 2^-48 is the unit
 roundoff of a double word:
   u: 1e-12.  The FFT's error is normwise, ~u^2 log2(n) (measured <= 6e-14 up to 2048^2).
-  dw/dt: max(1e-12, 4 u^2 (0.95 n / 2 pi + 4.4 mu n^2 |w| / |dw/dt|)), n = the larger side.
-    Phi and w are stored and formed with ~4 u^2 relative rounding per node, independently from
-    node to node; the 4th-order first difference amplifies such noise by its coefficient norm
+  dw/dt: max(1e-12, (4 + 2 log2 N) u^2 0.95 n / 2 pi + 4 u^2 4.4 mu n^2 |w| / |dw/dt|),
+    n = the larger side, N = n1 n2.  Phi and w are stored and formed with ~4 u^2 relative
+    rounding per node, and Phi holds |u|^2 / 2, whose relative error is twice the velocity's:
+    the FFT's normwise ~u^2 log2 N (measured 1.2-1.8 u^2 log2 N); these errors vary from node to
+    node, and the 4th-order first difference amplifies such noise by its coefficient norm
     0.95 / dx = 0.95 n (relative to |D Phi| >= 2 pi |Phi| for the lowest mode), the Laplacian
-    (two axes) by 4.4 / dx^2.  So at 4096^2 the bound is ~9e-12 where the FP64 path stays
-    at 1e-12: 48 bits are 5 fewer than FP64's 53.
+    (two axes) by 4.4 / dx^2.  So at 4096^2 the bound is ~1e-10 where the FP64 path stays at
+    1e-12: 48 bits are 5 fewer than FP64's 53, and the long stencil axis multiplies them.
   stepped state: 1e-12 on z and w, 1e-10 on the displacement z - z0 (as for the FP64 path).
 z1 and z2 are stored relative to the mesh coordinates, so the amplification acts on the
 perturbation, not on the coordinate.
@@ -27,8 +29,9 @@ U2 = 2.0 ** -48
 
 
 def wdot_tol(n, mu, w, wd_ref):
+    N = w.shape[-1]
     ratio = np.linalg.norm(w) / max(np.linalg.norm(wd_ref), 1e-300)
-    return max(TOL, 4 * U2 * (0.95 * n / (2 * np.pi) + 4.4 * mu * n * n * ratio))
+    return max(TOL, (4 + 2 * np.log2(N)) * U2 * 0.95 * n / (2 * np.pi) + 4 * U2 * 4.4 * mu * n * n * ratio)
 
 
 def rel(a, b):

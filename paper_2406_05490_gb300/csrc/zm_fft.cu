@@ -141,44 +141,47 @@ __device__ void fft_dit(double2 *x, int rows, int L, const double2 *__restrict__
 }
 
 // DFT of length R (odd) in registers, v[t] -> sum_t v[t] W_R^(t k), W_R = exp(sgn 2 pi i / R),
-// from the half table of W_L (W_R^e = W_L^(e M)).  Outputs k and R - k share the sums
-// A_k = v0 + sum_n (v_n + v_{R-n}) Re W^(nk) and B_k = sum_n (v_n - v_{R-n}) Im W^(nk):
-// X_k = A_k + i B_k, X_{R-k} = A_k - i B_k (W^(n(R-k)) is the conjugate of W^(nk)).
-template <int R>
+// from the half table of W_L (W_R^e = W_L^(e M)); output k goes to out(k, X_k).  v is
+// overwritten by the sums s_n = v_n + v_{R-n} and differences d_n = v_n - v_{R-n}: outputs k
+// and R - k share A_k = v0 + sum_n s_n Re W^(nk) and B_k = sum_n d_n Im W^(nk), as
+// X_k = A_k + i B_k and X_{R-k} = A_k - i B_k (W^(n(R-k)) is the conjugate of W^(nk)).
+template <int R, class Out>
 __device__ __forceinline__ void dft_small(double2 (&v)[R], const double2 *__restrict__ twl, int M, int half,
-                                          int sgn)
+                                          int sgn, Out out)
 {
     constexpr int H = (R - 1) / 2;
-    double2 sm[H], df[H];
     double2 x0 = v[0];
 #pragma unroll
     for (int n = 1; n <= H; ++n) {
-        sm[n - 1] = cadd(v[n], v[R - n]);
-        df[n - 1] = csub(v[n], v[R - n]);
-        x0 = cadd(x0, sm[n - 1]);
+        const double2 a = v[n], b = v[R - n];
+        v[n] = cadd(a, b);
+        v[R - n] = csub(a, b);
+        x0 = cadd(x0, v[n]);
     }
-#pragma unroll
-    for (int k = 1; k <= H; ++k) {
+    out(0, x0);
+#pragma unroll 1
+    for (int k = 1; k <= H; ++k) {  // not unrolled: keeps the live registers to v and two sums
         double2 a = v[0], b = make_double2(0.0, 0.0);
 #pragma unroll
         for (int n = 1; n <= H; ++n) {
             const double2 w = twiddle(twl, ((n * k) % R) * M, half, sgn);
-            a.x = fma(sm[n - 1].x, w.x, a.x);
-            a.y = fma(sm[n - 1].y, w.x, a.y);
-            b.x = fma(df[n - 1].x, w.y, b.x);
-            b.y = fma(df[n - 1].y, w.y, b.y);
+            a.x = fma(v[n].x, w.x, a.x);
+            a.y = fma(v[n].y, w.x, a.y);
+            b.x = fma(v[R - n].x, w.y, b.x);
+            b.y = fma(v[R - n].y, w.y, b.y);
         }
-        v[k] = make_double2(a.x - b.y, a.y + b.x);      // a + i b
-        v[R - k] = make_double2(a.x + b.y, a.y - b.x);  // a - i b
+        out(k, make_double2(a.x - b.y, a.y + b.x));      // a + i b
+        out(R - k, make_double2(a.x + b.y, a.y - b.x));  // a - i b
     }
-    v[0] = x0;
 }
 
 // Radix-R stage of decimation in frequency on `rows` rows of length L = R M in shared memory:
 // for each n1 < M the values x[n1 + M t] (t < R) become W_L^(n1 k) DFT_R(x)[k] at n1 + M k, so
 // that sub-row k (positions k M .. k M + M - 1) transforms, with length M, to outputs R k1 + k.
+// Not inlined: each radix is compiled once per pass kernel instead of once per call site.
 template <int R>
-__device__ void radix_dif_r(double2 *x, int rows, int M, int lM, const double2 *__restrict__ twl, int sgn)
+__device__ __noinline__ void radix_dif_r(double2 *x, int rows, int M, int lM, const double2 *__restrict__ twl,
+                                         int sgn)
 {
     const int L = R * M, half = L >> 1;
     for (int b = threadIdx.x; b < rows * M; b += blockDim.x) {
@@ -187,19 +190,19 @@ __device__ void radix_dif_r(double2 *x, int rows, int M, int lM, const double2 *
         double2 v[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) v[t] = xr[t * M];
-        dft_small<R>(v, twl, M, half, sgn);
-        xr[0] = v[0];
-#pragma unroll
-        for (int k = 1; k < R; ++k) xr[k * M] = n1 ? cmul(v[k], twiddle(twl, n1 * k, half, sgn)) : v[k];
+        dft_small<R>(v, twl, M, half, sgn, [&](int k, double2 val) {
+            xr[k * M] = (n1 && k) ? cmul(val, twiddle(twl, n1 * k, half, sgn)) : val;
+        });
     }
     __syncthreads();
 }
 
 // The mirror stage of decimation in time: sub-row k holds, in natural order n1, the length-M
 // transform of the outputs R k1 + k; the values x[k M + n1] times W_L^(n1 k) go through DFT_R
-// over k, and output t lands at n1 + M t.
+// over k, and output t lands at n1 + M t (in place: each thread owns its column n1).
 template <int R>
-__device__ void radix_dit_r(double2 *x, int rows, int M, int lM, const double2 *__restrict__ twl, int sgn)
+__device__ __noinline__ void radix_dit_r(double2 *x, int rows, int M, int lM, const double2 *__restrict__ twl,
+                                         int sgn)
 {
     const int L = R * M, half = L >> 1;
     for (int b = threadIdx.x; b < rows * M; b += blockDim.x) {
@@ -209,9 +212,7 @@ __device__ void radix_dit_r(double2 *x, int rows, int M, int lM, const double2 *
         v[0] = xr[0];
 #pragma unroll
         for (int k = 1; k < R; ++k) v[k] = n1 ? cmul(xr[k * M], twiddle(twl, n1 * k, half, sgn)) : xr[k * M];
-        dft_small<R>(v, twl, M, half, sgn);
-#pragma unroll
-        for (int t = 0; t < R; ++t) xr[t * M] = v[t];
+        dft_small<R>(v, twl, M, half, sgn, [&](int t, double2 val) { xr[t * M] = val; });
     }
     __syncthreads();
 }
@@ -289,7 +290,7 @@ __device__ __forceinline__ int dif_freq(int pos, const Side &s)
 
 // pass A: rows i of length n2 from w1 + i w2; forward; write out[j][i] (transposed).
 template <bool kMix>
-__global__ void __launch_bounds__(kFftTpb)
+__global__ void __launch_bounds__(kFftTpb, kMix ? 2 : 1)
     pass_a(int n1, int n2, Side s2, int rows, const double *__restrict__ w, double2 *__restrict__ out)
 {
     extern __shared__ double2 sx[];
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(kFftTpb)
 
 // pass B: rows j (length n1) of the transpose; forward; multiply; inverse; write out[i][j].
 template <bool kMix>
-__global__ void __launch_bounds__(kFftTpb)
+__global__ void __launch_bounds__(kFftTpb, kMix ? 2 : 1)
     pass_b(int n1, int n2, Side s1, int rows, double invL1, double invL2, const double2 *__restrict__ in,
            double2 *__restrict__ out)
 {
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(kFftTpb)
 
 // pass C: rows i (length n2); inverse; s = Re / (n1 n2); u = -s/2 N; Phi = q + |u|^2 / 2.
 template <bool kMix>
-__global__ void __launch_bounds__(kFftTpb)
+__global__ void __launch_bounds__(kFftTpb, kMix ? 2 : 1)
     pass_c(int n1, int n2, Side s2, int rows, double inv, const double2 *__restrict__ in,
            const double *__restrict__ nrm, const double *__restrict__ q, double *__restrict__ u,
            double *__restrict__ phi)

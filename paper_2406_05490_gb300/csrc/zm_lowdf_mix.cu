@@ -145,7 +145,7 @@ __device__ __forceinline__ int mix_pos(int f, int R)
 
 // pass A on rows of length n2 = R 2^A.
 template <int A>
-__global__ void __launch_bounds__(kMixTpb, 1)
+__global__ void __launch_bounds__(kMixTpb, 2)
     pass_a_dfm(int n1, int R, int lr, const float2 *__restrict__ w, const ulonglong2 *__restrict__ tw2,
                const ulonglong2 *__restrict__ twl2, ulonglong2 *__restrict__ out)
 {
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kMixTpb, 1)
 
 // pass B on columns of length n1 = R 2^A.
 template <int A>
-__global__ void __launch_bounds__(kMixTpb, 1)
+__global__ void __launch_bounds__(kMixTpb, 2)
     pass_b_dfm(int n2, int R, int lr, Dc invL1, Dc invL2, const ulonglong2 *__restrict__ in,
                const ulonglong2 *__restrict__ tw1, const ulonglong2 *__restrict__ twl1, ulonglong2 *__restrict__ out)
 {
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kMixTpb, 1)
 
 // pass C on rows of length n2 = R 2^A.
 template <int A>
-__global__ void __launch_bounds__(kMixTpb, 1)
+__global__ void __launch_bounds__(kMixTpb, 2)
     pass_c_dfm(int n1, int R, int lr, Dc scale, const ulonglong2 *__restrict__ in,
                const ulonglong2 *__restrict__ tw2, const ulonglong2 *__restrict__ twl2, const float2 *__restrict__ nrm,
                const float2 *__restrict__ q, float2 *__restrict__ u, float2 *__restrict__ phi)

@@ -386,6 +386,7 @@ int zm_get_state(zm_ctx *c, double *z, double *w)
 int zm_velocity(zm_ctx *c, const double *z, const double *w, double *u, double *wdot)
 {
     if (!c || !u) return set_error(ZM_ERR_INVALID, "zm_velocity: null context or u");
+    const NvtxRange range("zm_velocity");
     if ((z == nullptr) != (w == nullptr))
         return set_error(ZM_ERR_INVALID, "zm_velocity: give both z and w, or neither");
     const size_t N = c->geom.N;
@@ -467,6 +468,7 @@ static zm_profile step_counts(const zm_ctx *c)
 int zm_step(zm_ctx *c, double dt, int nsteps)
 {
     if (!c) return set_error(ZM_ERR_INVALID, "zm_step: null context");
+    const NvtxRange range("zm_step");
     if (!std::isfinite(dt) || nsteps < 0)
         return set_error(ZM_ERR_INVALID, "zm_step: dt must be finite and nsteps >= 0");
     if (c->batch && c->order == ZM_ORDER_HIGH) {

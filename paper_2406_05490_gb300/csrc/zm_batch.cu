@@ -773,6 +773,7 @@ int zm_batch_get_state(zm_batch *bt, int32_t index, double *z, double *w)
 int zm_batch_velocity(zm_batch *bt)
 {
     if (!bt) return set_error(ZM_ERR_INVALID, "zm_batch_velocity: null batch");
+    const NvtxRange range("zm_batch_velocity");
     int rc = bt->b.derivative(0, bt->b.stream);
     if (!rc) rc = bt->b.vorticity(0, 0, 0, 0, 0, bt->b.stream);
     return rc;
@@ -794,6 +795,7 @@ int zm_batch_get_velocity(zm_batch *bt, int32_t index, double *u, double *wdot)
 int zm_batch_step(zm_batch *bt, double dt, int32_t nsteps)
 {
     if (!bt || !std::isfinite(dt) || nsteps < 0) return set_error(ZM_ERR_INVALID, "zm_batch_step: bad arguments");
+    const NvtxRange range("zm_batch_step");
     int rc = bt->b.set_dt(dt);
     return rc ? rc : bt->b.step(nsteps, true);
 }

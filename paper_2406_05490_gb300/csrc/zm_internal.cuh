@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -11,6 +12,16 @@
 #include "zm.h"
 
 namespace zm {
+
+// A named NVTX range over one host call (zm_step, zm_velocity, the batch and server steps), so
+// that a profiler's timeline and ncu's --nvtx filters can attribute kernels to API calls.  NVTX3
+// is header-only and costs a branch when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Mesh constants handed to every stencil kernel by value.
 struct Geom {

@@ -186,7 +186,11 @@ public:
             if (any_work) {
                 // plain launches right after a membership change; once the same set has run an
                 // iteration, the step is captured as a graph and replayed until the set changes
-                int rc = batch.step(1, stable >= 1);
+                int rc;
+                {
+                    const NvtxRange range("zm_server_iteration");
+                    rc = batch.step(1, stable >= 1);
+                }
                 if (rc) {
                     fail_all(rc);
                     continue;

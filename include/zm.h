@@ -184,6 +184,19 @@ int zm_wait_selftest(int64_t max_polls, int32_t arrive, double *elapsed_ms);
 /* The poll limit of the library's bounded waits (the kernels give up after this many polls). */
 int64_t zm_wait_poll_limit(void);
 
+/* 1 when this library is the checked build (libzm_checked.so, compiled with ZM_CHECKS=1), else 0.
+ * In the checked build every kernel tests the indices it computes (neighbour wraps, tile and
+ * record numbers, transposed writes, shared-memory positions) before the access; an index
+ * outside its array is counted and the access skipped, so the kernel neither faults nor traps.
+ * Compute-sanitizer is not needed for this; the default build has no such tests. */
+int zm_checked_build(void);
+
+/* Index violations the checked build has counted since the last clear, over all kernels:
+ * *hits (required) the count, *first_index and *source_line (may be NULL) the first offending
+ * index and the source line of its test.  clear != 0 resets the count.  Synchronises the device.
+ * Returns ZM_OK (with *hits = 0 in the default build), or ZM_ERR_CUDA. */
+int zm_bounds_status(uint32_t *hits, int64_t *first_index, int32_t *source_line, int32_t clear);
+
 /* ---- batches of interfaces (high order, FP32C) ------------------------------------------- */
 
 /* Many independent interfaces of uneven mesh sizes advanced together: each RK3 stage runs four

@@ -1,8 +1,10 @@
 """Build libzm.so (the CUDA C-ABI library) in-tree for sm_103a.
 
 Each translation unit under csrc/ is compiled in parallel with nvcc into _build/, then linked
-into paper_2406_05490_gb300/_lib/libzm.so.  Rebuilds only what changed (source or header newer
-than its object).
+into paper_2406_05490_gb300/_lib/libzm.so.  The checked build of the same sources (-DZM_CHECKS=1:
+kernels test their computed indices and count violations instead of accessing out of range)
+goes through _build_checked/ into _lib/libzm_checked.so, in the same pool of compile jobs.
+Rebuilds only what changed (source or header newer than its object).
 """
 from __future__ import annotations
 
@@ -17,8 +19,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
+OBJDIR_CHECKED = os.path.join(PKG, "_build_checked")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libzm.so")
+LIB_CHECKED = os.path.join(LIBDIR, "libzm_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -36,14 +40,15 @@ def _headers():
     return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def _compile(src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
+def _compile(src: str, verbose_ptxas: bool, checked: bool = False) -> str:
+    obj = os.path.join(OBJDIR_CHECKED if checked else OBJDIR, os.path.basename(src) + ".o")
     newest = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest and not verbose_ptxas:
         return obj
-    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj + ".tmp"]
+    flags = NVCC_FLAGS + (["-DZM_CHECKS=1"] if checked else [])
+    cmd = [_nvcc(), *ARCH, *flags, "-c", src, "-o", obj + ".tmp"]
     if src.endswith(".cpp"):
-        cmd = [_nvcc(), *NVCC_FLAGS, "-x", "c++", "-c", src, "-o", obj + ".tmp"]
+        cmd = [_nvcc(), *flags, "-x", "c++", "-c", src, "-o", obj + ".tmp"]
     if verbose_ptxas:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -55,19 +60,29 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     return obj
 
 
-def build(verbose_ptxas: bool = False) -> str:
-    os.makedirs(OBJDIR, exist_ok=True)
-    os.makedirs(LIBDIR, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
-    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs))
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+def _link(lib: str, objs) -> None:
+    if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
+
+
+def build(verbose_ptxas: bool = False, checked: bool = True) -> str:
+    """Build libzm.so (and, unless checked=False, libzm_checked.so); returns libzm.so's path."""
+    for d in (OBJDIR, OBJDIR_CHECKED, LIBDIR):
+        os.makedirs(d, exist_ok=True)
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+    jobs = [(s, False) for s in srcs] + ([(s, True) for s in srcs] if checked else [])
+    # the slowest units first, so that the pool's tail is short
+    jobs.sort(key=lambda j: -os.path.getsize(j[0]))
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(lambda j: (j[1], _compile(j[0], verbose_ptxas and not j[1], j[1])), jobs))
+    _link(LIB, sorted(o for c, o in objs if not c))
+    if checked:
+        _link(LIB_CHECKED, sorted(o for c, o in objs if c))
     return LIB
 
 

@@ -174,6 +174,8 @@ static int read_status(zm_ctx *c)
     return ZM_OK;
 }
 
+ZM_BOUNDS_READER(bounds_api)
+
 }  // namespace zm
 
 using namespace zm;

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(kPtb)
 {
     const Inst &I = insts[block_inst[blockIdx.x]];
     const int p = (blockIdx.x - I.block0) * kPtb + threadIdx.x;
-    if (p >= I.geom.N) return;
+    if (p >= I.geom.N || !ZM_IDX_OK(p, I.geom.N)) return;
     const double pref = I.geom.dx1 * I.geom.dx2 / (4.0 * 3.14159265358979323846);
     geometry_point<kGeoFp32c>(I.geom, I.tiling, p, I.y[yin], pref, I.g, (float)(I.delta * I.delta),
                               I.near_rec, I.far_rec, I.tinfo, I.gmax, I.q, nullptr);
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kPtb)
     if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0ull;
     const Inst &I = insts[block_inst[blockIdx.x]];
     const int p = (blockIdx.x - I.block0) * kPtb + threadIdx.x;
-    if (p >= I.geom.N) return;
+    if (p >= I.geom.N || !ZM_IDX_OK(p, I.geom.N)) return;
     const size_t N = I.geom.N;
     const double inv = ldexp(1.0, -*I.scale);
     double s[3];
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kPtb)
 {
     const Inst &I = insts[block_inst[blockIdx.x]];
     const int p = (blockIdx.x - I.block0) * kPtb + threadIdx.x;
-    if (p >= I.geom.N) return;
+    if (p >= I.geom.N || !ZM_IDX_OK(p, I.geom.N)) return;
     if (I.mu != 0.0)
         vorticity_point<true, kMode>(I.geom, p, I.phi, I.y[yin], I.u, I.atwood, I.mu, I.dt, ca, cb,
                                      I.y[0], I.y[yout], I.y[2]);
@@ -675,6 +675,8 @@ int batch_autotune_tiles(Batch *b, const char *path, int *tp1, int *tp2, int *ch
     if (tp2) *tp2 = kShapes[k][1];
     return rc;
 }
+
+ZM_BOUNDS_READER(bounds_batch)
 
 }  // namespace zm
 

@@ -49,6 +49,10 @@ __global__ void __launch_bounds__(kTpb)
         t0 = blockIdx.y * tiles_per_split;
         nt = max(0, min(ntiles, t0 + tiles_per_split) - t0);
     }
+    // checked build: every tile this CTA copies must exist, and the source slice lie in a tile
+    if (nt > 0 && (!ZM_IDX_OK(t0, ntiles) || !ZM_IDX_OK(t0 + nt - 1, ntiles) || !ZM_IDX_OK(j0, kTs) ||
+                   !ZM_IDX_OK(j1 - 1, kTs)))
+        nt = 0;
 
     double tx[kR], ty[kR], tz[kR], ax[kR], ay[kR], az[kR];
 #pragma unroll
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(kTpb)
 #pragma unroll
     for (int r = 0; r < kR; ++r) {
         const int p = blockIdx.x * kTpb * kR + r * kTpb + tid;
-        if (p < N) {
+        if (p < N && ZM_IDX_OK(p, N)) {
             double *o = part + (size_t)blockIdx.y * 3 * N;
             o[p] = ax[r];
             o[(size_t)N + p] = ay[r];
@@ -292,6 +296,8 @@ bool on_device(const void *p)
 }
 
 }  // namespace
+ZM_BOUNDS_READER(bounds_br)
+
 }  // namespace zm
 
 extern "C" int zm_br_velocity_noalloc(int32_t n, const double *z, const double *gamma,

@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
                     if (insts[mid].item0 <= it) lo = mid;
                     else hi = mid - 1;
                 }
+                if (!ZM_IDX_OK(lo, ninst)) continue;
                 const Inst &I = insts[lo];
                 const long long local = it - I.item0;
                 p_inst = lo;
@@ -230,6 +231,8 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
             const Inst &I = insts[p_inst];
             const int S = p_next++;
             --p_left;
+            // checked build: a tile number outside the interface's records is skipped
+            if (!ZM_IDX_OK(p_tile, I.tiling.ntiles) || !ZM_IDX_OK(S, I.tiling.ntiles)) continue;
             const float4 a = I.tinfo[p_tile], b = I.tinfo[S];
             const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
             const float D = sqrtf(dx * dx + dy * dy + dz * dz);
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
             const int slot = r * kT + tid;
             const int lg2 = __ffs(I.tiling.tp2) - 1;  // tp2 is a power of two
             const int i = ti * I.tiling.tp1 + (slot >> lg2), j = tj * I.tiling.tp2 + (slot & (I.tiling.tp2 - 1));
-            if (i < I.geom.n1 && j < I.geom.n2) {
+            if (i < I.geom.n1 && j < I.geom.n2 && ZM_IDX_OK((size_t)i * I.geom.n2 + j, N)) {
                 const size_t p = (size_t)i * I.geom.n2 + j;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -435,5 +438,7 @@ int launch_br32_batch(const Inst *d_insts, int ninst, long long nitems, int ctas
         br32_batch_kernel<false><<<ctas, kT, 0, s>>>(d_insts, ninst, nitems, counter, err);
     return cuda_check(cudaGetLastError(), "Birkhoff-Rott FP32C kernel launch");
 }
+
+ZM_BOUNDS_READER(bounds_br32)
 
 }  // namespace zm

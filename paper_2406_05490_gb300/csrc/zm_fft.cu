@@ -186,6 +186,7 @@ __device__ __noinline__ void radix_dif_r(double2 *x, int rows, int M, int lM, co
     const int L = R * M, half = L >> 1;
     for (int b = threadIdx.x; b < rows * M; b += blockDim.x) {
         const int row = b >> lM, n1 = b & (M - 1);
+        if (!ZM_IDX_OK(row, rows)) continue;
         double2 *xr = x + (size_t)row * L + n1;
         double2 v[R];
 #pragma unroll
@@ -207,6 +208,7 @@ __device__ __noinline__ void radix_dit_r(double2 *x, int rows, int M, int lM, co
     const int L = R * M, half = L >> 1;
     for (int b = threadIdx.x; b < rows * M; b += blockDim.x) {
         const int row = b >> lM, n1 = b & (M - 1);
+        if (!ZM_IDX_OK(row, rows)) continue;
         double2 *xr = x + (size_t)row * L + n1;
         double2 v[R];
         v[0] = xr[0];
@@ -299,13 +301,15 @@ __global__ void __launch_bounds__(kFftTpb, kMix ? 2 : 1)
     for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
         const int r = e / n2, j = e - r * n2;
         const size_t p = (size_t)(i0 + r) * n2 + j;
-        sx[e] = make_double2(w[p], w[N + p]);
+        sx[e] = ZM_IDX_OK(p, N) ? make_double2(w[p], w[N + p]) : make_double2(0.0, 0.0);
     }
     __syncthreads();
     side_dif<kMix>(sx, rows, s2, -1);
     for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
         const int j = e / rows, r = e - j * rows;
-        out[(size_t)j * n1 + i0 + r] = sx[(size_t)r * n2 + dif_pos<kMix>(j, s2)];
+        const size_t o = (size_t)j * n1 + i0 + r;
+        const int k = r * n2 + dif_pos<kMix>(j, s2);
+        if (ZM_IDX_OK(o, N) && ZM_IDX_OK(k, rows * n2)) out[o] = sx[k];
     }
 }
 
@@ -317,7 +321,8 @@ __global__ void __launch_bounds__(kFftTpb, kMix ? 2 : 1)
 {
     extern __shared__ double2 sx[];
     const int j0 = blockIdx.x * rows;
-    for (int e = threadIdx.x; e < rows * n1; e += blockDim.x) sx[e] = in[(size_t)j0 * n1 + e];
+    for (int e = threadIdx.x; e < rows * n1; e += blockDim.x)
+        sx[e] = ZM_IDX_OK((size_t)j0 * n1 + e, (size_t)n1 * n2) ? in[(size_t)j0 * n1 + e] : make_double2(0.0, 0.0);
     __syncthreads();
     side_dif<kMix>(sx, rows, s1, -1);
     for (int e = threadIdx.x; e < rows * n1; e += blockDim.x) {
@@ -339,7 +344,7 @@ __global__ void __launch_bounds__(kFftTpb, kMix ? 2 : 1)
     side_dit<kMix>(sx, rows, s1, +1);
     for (int e = threadIdx.x; e < rows * n1; e += blockDim.x) {
         const int i = e / rows, r = e - i * rows;
-        out[(size_t)i * n2 + j0 + r] = sx[(size_t)r * n1 + i];
+        if (ZM_IDX_OK((size_t)i * n2 + j0 + r, (size_t)n1 * n2)) out[(size_t)i * n2 + j0 + r] = sx[(size_t)r * n1 + i];
     }
 }
 
@@ -353,13 +358,16 @@ __global__ void __launch_bounds__(kFftTpb, kMix ? 2 : 1)
     extern __shared__ double2 sx[];
     const int i0 = blockIdx.x * rows;
     const size_t N = (size_t)n1 * n2;
-    for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) sx[e] = in[(size_t)i0 * n2 + e];
+    for (int e = threadIdx.x; e < rows * n2; e += blockDim.x)
+        sx[e] = ZM_IDX_OK((size_t)i0 * n2 + e, N) ? in[(size_t)i0 * n2 + e] : make_double2(0.0, 0.0);
     __syncthreads();
     side_dif<kMix>(sx, rows, s2, +1);
     for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
         const int r = e / n2, j = e - r * n2;
         const size_t p = (size_t)(i0 + r) * n2 + j;
-        const double s = sx[(size_t)r * n2 + dif_pos<kMix>(j, s2)].x * inv;
+        const int k = r * n2 + dif_pos<kMix>(j, s2);
+        if (!ZM_IDX_OK(p, N) || !ZM_IDX_OK(k, rows * n2)) continue;
+        const double s = sx[k].x * inv;
         const double ux = -0.5 * s * nrm[p], uy = -0.5 * s * nrm[N + p], uz = -0.5 * s * nrm[2 * N + p];
         u[p] = ux;
         u[N + p] = uy;
@@ -497,5 +505,7 @@ int launch_riesz(zm_ctx *c, const double *y)
     c->prof.acc.launches[ZM_K_FFT] += 2;  // three kernels per Riesz evaluation
     return cuda_check(cudaGetLastError(), "Riesz FFT launch");
 }
+
+ZM_BOUNDS_READER(bounds_fft)
 
 }  // namespace zm

@@ -230,6 +230,74 @@ int derivative(zm_ctx *c, const double *y);
 // ---- device helpers ------------------------------------------------------------------------------
 #ifdef __CUDACC__
 namespace zm {
+// ---- the checked build ------------------------------------------------------------------------
+// Compiled with -DZM_CHECKS=1 (libzm_checked.so), the kernels test the indices they compute
+// (gathers, wraps, tile and record numbers, transposed writes, shared-memory positions) before
+// each access; an index outside its array is counted, the first one recorded, and the access
+// skipped, so that the kernel neither faults nor traps.  zm_bounds_status() reads the counts.
+// In the default build ZM_IDX_OK is the constant true and the tests compile away.
+#ifndef ZM_CHECKS
+#define ZM_CHECKS 0
+#endif
+
+#if ZM_CHECKS
+namespace chk {
+// one count per translation unit (device globals have internal linkage here), summed by the
+// host readers below
+static __device__ unsigned int g_hits;
+static __device__ long long g_first;
+static __device__ int g_site;
+
+static __device__ __noinline__ bool fail(long long i, int site)
+{
+    if (atomicAdd(&g_hits, 1u) == 0) {
+        g_first = i;
+        g_site = site;
+    }
+    return false;
+}
+}  // namespace chk
+#define ZM_IDX_OK(i, n) \
+    ((long long)(i) >= 0 && (long long)(i) < (long long)(n) ? true : ::zm::chk::fail((long long)(i), __LINE__))
+// Host side: adds this unit's counts to *hits (the first offending index and source line to
+// *first, *site when none was recorded yet) and clears them when `clear`.
+#define ZM_BOUNDS_READER(name)                                                                    \
+    int name(unsigned int *hits, long long *first, int *site, int clear)                          \
+    {                                                                                             \
+        unsigned int h = 0;                                                                       \
+        long long f = -1;                                                                         \
+        int l = 0;                                                                                \
+        if (cudaMemcpyFromSymbol(&h, chk::g_hits, sizeof(h)) != cudaSuccess ||                    \
+            cudaMemcpyFromSymbol(&f, chk::g_first, sizeof(f)) != cudaSuccess ||                    \
+            cudaMemcpyFromSymbol(&l, chk::g_site, sizeof(l)) != cudaSuccess)                       \
+            return -1;                                                                            \
+        if (h && *hits == 0) {                                                                    \
+            *first = f;                                                                           \
+            *site = l;                                                                            \
+        }                                                                                         \
+        *hits += h;                                                                               \
+        if (clear) {                                                                              \
+            const unsigned int z = 0;                                                             \
+            if (cudaMemcpyToSymbol(chk::g_hits, &z, sizeof(z)) != cudaSuccess) return -1;         \
+        }                                                                                         \
+        return 0;                                                                                 \
+    }
+#else
+#define ZM_IDX_OK(i, n) true
+#define ZM_BOUNDS_READER(name) \
+    int name(unsigned int *, long long *, int *, int) { return 0; }
+#endif
+
+// Readers of the translation units with kernels (zero work in the default build).
+int bounds_api(unsigned int *, long long *, int *, int);
+int bounds_batch(unsigned int *, long long *, int *, int);
+int bounds_br(unsigned int *, long long *, int *, int);
+int bounds_br32(unsigned int *, long long *, int *, int);
+int bounds_fft(unsigned int *, long long *, int *, int);
+int bounds_lowdf(unsigned int *, long long *, int *, int);
+int bounds_lowdf_mix(unsigned int *, long long *, int *, int);
+int bounds_stencil(unsigned int *, long long *, int *, int);
+
 namespace dev {
 
 // Bounded waits: every spin on an mbarrier gives up after this many polls and reports

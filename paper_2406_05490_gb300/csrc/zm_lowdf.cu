@@ -86,6 +86,12 @@ __device__ __forceinline__ Nb nb_axis1(int i, int j, const DfGeo &g)
     return Nb{r + wrap(j, -2, g.n2), r + wrap(j, -1, g.n2), r + wrap(j, 1, g.n2), r + wrap(j, 2, g.n2)};
 }
 
+// Checked build: every neighbour index lies in the mesh.
+__device__ __forceinline__ bool nb_ok(const Nb &n, int N)
+{
+    return ZM_IDX_OK(n.m2, N) && ZM_IDX_OK(n.m1, N) && ZM_IDX_OK(n.p1, N) && ZM_IDX_OK(n.p2, N);
+}
+
 // (f-2 - f+2) + 8 (f+1 - f-1): 12 dx times the 4th-order first difference
 __device__ __forceinline__ df diff1_s(const float2 *__restrict__ f, const Nb &n)
 {
@@ -123,6 +129,7 @@ __global__ void __launch_bounds__(kTpb)
     node_ij<kP2>(p, g, i, j);
     const int N = g.N;
     const Nb na = nb_axis0<kP2>(i, j, g), nb = nb_axis1<kP2>(i, j, g);
+    if (!nb_ok(na, N) || !nb_ok(nb, N)) return;  // checked build only
     df b1[3], b2[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -164,6 +171,7 @@ __global__ void __launch_bounds__(kTpb)
     node_ij<kP2>(p, g, i, j);
     const int N = g.N;
     const Nb na = nb_axis0<kP2>(i, j, g), nb = nb_axis1<kP2>(i, j, g);
+    if (!nb_ok(na, N) || !nb_ok(nb, N)) return;  // checked build only
     const df m2a = dc(g.m2a);
     df f1 = mul(m2a, diff1_df(phi, na, dc(g.i12a)));
     df f2 = mul(m2a, diff1_df(phi, nb, dc(g.i12b)));
@@ -199,6 +207,7 @@ __global__ void __launch_bounds__(threads_for(L), minb_for(L))
     extern __shared__ ulonglong2 sx[];
     const int rows = 1 << lr;
     const int i0 = blockIdx.x * rows;
+    if (!ZM_IDX_OK(i0 + rows - 1, n1)) return;  // checked build: the CTA's rows exist
     const size_t N = (size_t)n1 << L;
     const float2 *w1 = w + ((size_t)i0 << L), *w2 = w1 + N;
     auto ldg = [&](int row, int i) { return ld2(c2_pack(w1[(row << L) + i], w2[(row << L) + i])); };
@@ -219,6 +228,7 @@ __global__ void __launch_bounds__(threads_for(L), minb_for(L))
     constexpr int NC = nc_of(L);
     const int rows = 1 << lr;
     const int j0 = blockIdx.x * rows;
+    if (!ZM_IDX_OK(j0 + rows - 1, n2)) return;  // checked build: the CTA's columns exist
     const ulonglong2 *src = in + ((size_t)j0 << L);
     if constexpr (NC == 1) {  // the whole transform is the middle group: stage the rows first
         for (int e = threadIdx.x; e < (rows << L); e += blockDim.x) sx[phys(e)] = src[e];
@@ -246,6 +256,7 @@ __global__ void __launch_bounds__(threads_for(L), minb_for(L))
     extern __shared__ ulonglong2 sx[];
     const int rows = 1 << lr;
     const int i0 = blockIdx.x * rows;
+    if (!ZM_IDX_OK(i0 + rows - 1, n1)) return;  // checked build: the CTA's rows exist
     const size_t N = (size_t)n1 << L;
     const size_t o = (size_t)i0 << L;
     const ulonglong2 *src = in + o;
@@ -551,5 +562,7 @@ int df_check_finite(zm_ctx *c, const double *y, size_t nvalues, int *dev_flag)
     finite_f32_kernel<<<4 * 152, kTpb, 0, c->stream>>>(2 * nvalues, reinterpret_cast<const float *>(y), dev_flag);
     return cuda_check(cudaGetLastError(), "finite check launch");
 }
+
+ZM_BOUNDS_READER(bounds_lowdf)
 
 }  // namespace zm

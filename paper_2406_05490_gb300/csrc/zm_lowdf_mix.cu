@@ -75,6 +75,7 @@ __device__ __noinline__ void radix_dif_df(ulonglong2 *sx, int rows, int lM, cons
     const int M = 1 << lM, L = R * M, half = L >> 1;
     for (int b = threadIdx.x; b < rows * M; b += blockDim.x) {
         const int row = b >> lM, n1 = b & (M - 1);
+        if (!ZM_IDX_OK(row, rows)) continue;
         const int base = row * L + n1;
         C2 v[R];
 #pragma unroll
@@ -94,6 +95,7 @@ __device__ __noinline__ void radix_dit_df(ulonglong2 *sx, int rows, int lM, cons
     const int M = 1 << lM, L = R * M, half = L >> 1;
     for (int b = threadIdx.x; b < rows * M; b += blockDim.x) {
         const int row = b >> lM, n1 = b & (M - 1);
+        if (!ZM_IDX_OK(row, rows)) continue;
         const int base = row * L + n1;
         C2 v[R];
         v[0] = ld2(sx[phys(base)]);
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(kMixTpb, 2)
     extern __shared__ ulonglong2 sx[];
     const int L = R << A, rows = 1 << lr;
     const int i0 = blockIdx.x * rows;
+    if (!ZM_IDX_OK(i0 + rows - 1, n1)) return;  // checked build: the CTA's rows exist
     const size_t N = (size_t)n1 * L;
     const float2 *w1 = w + (size_t)i0 * L, *w2 = w1 + N;
     radix_dif_any(sx, rows, R, A, twl2, -1, w1, w2, nullptr);
@@ -173,6 +176,7 @@ __global__ void __launch_bounds__(kMixTpb, 2)
     constexpr int NC = nc_of(A);
     const int L = R << A, rows = 1 << lr;
     const int j0 = blockIdx.x * rows;
+    if (!ZM_IDX_OK(j0 + rows - 1, n2)) return;  // checked build: the CTA's columns exist
     radix_dif_any(sx, rows, R, A, twl1, -1, nullptr, nullptr, in + (size_t)j0 * L);
     if constexpr (NC > 1) {
         auto lds = [&](int row, int i) { return ld2(sx[phys((row << A) + i)]); };
@@ -198,6 +202,7 @@ __global__ void __launch_bounds__(kMixTpb, 2)
     extern __shared__ ulonglong2 sx[];
     const int L = R << A, rows = 1 << lr;
     const int i0 = blockIdx.x * rows;
+    if (!ZM_IDX_OK(i0 + rows - 1, n1)) return;  // checked build: the CTA's rows exist
     const size_t N = (size_t)n1 * L;
     const size_t o = (size_t)i0 * L;
     radix_dif_any(sx, rows, R, A, twl2, +1, nullptr, nullptr, in + o);
@@ -270,5 +275,7 @@ int df_mix_pass_c(int A, int n1, int R, int lr, size_t smem, cudaStream_t s, dou
         return FftLaunchMix<decltype(lc)::value>::c(n1, R, lr, smem, s, split(scale), in, tw2, twl2, nrm, q, u, phi);
     });
 }
+
+ZM_BOUNDS_READER(bounds_lowdf_mix)
 
 }  // namespace zm

@@ -192,6 +192,25 @@ extern "C" int zm_wait_selftest(int64_t max_polls, int32_t arrive, double *elaps
 
 extern "C" int64_t zm_wait_poll_limit(void) { return (int64_t)dev::kSpinLimit; }
 
+extern "C" int zm_checked_build(void) { return ZM_CHECKS ? 1 : 0; }
+
+extern "C" int zm_bounds_status(uint32_t *hits, int64_t *first_index, int32_t *source_line, int32_t clear)
+{
+    if (!hits) return set_error(ZM_ERR_INVALID, "zm_bounds_status: null hits");
+    if (cudaDeviceSynchronize() != cudaSuccess) return set_error(ZM_ERR_CUDA, "zm_bounds_status: device error");
+    unsigned int h = 0;
+    long long f = -1;
+    int line = 0;
+    int (*const readers[])(unsigned int *, long long *, int *, int) = {
+        bounds_api, bounds_batch, bounds_br, bounds_br32, bounds_fft, bounds_lowdf, bounds_lowdf_mix, bounds_stencil};
+    for (auto rd : readers)
+        if (rd(&h, &f, &line, clear ? 1 : 0) != 0) return set_error(ZM_ERR_CUDA, "zm_bounds_status: read failed");
+    *hits = h;
+    if (first_index) *first_index = h ? f : -1;
+    if (source_line) *source_line = h ? line : 0;
+    return ZM_OK;
+}
+
 extern "C" int zm_measure_peak(int kind, double *ops_per_s)
 {
     if (!ops_per_s || kind < 0 || kind > 4) return set_error(ZM_ERR_INVALID, "zm_measure_peak: bad argument");

@@ -135,4 +135,6 @@ int launch_vorticity(zm_ctx *c, const double *y, double *wdot_out, const double 
     return cuda_check(cudaGetLastError(), "vorticity kernel launch");
 }
 
+ZM_BOUNDS_READER(bounds_stencil)
+
 }  // namespace zm

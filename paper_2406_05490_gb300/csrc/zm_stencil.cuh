@@ -27,10 +27,11 @@ __device__ __forceinline__ void line5(const double *__restrict__ f, int i, int j
         if (c >= 0 && c < n) {
             v[k] = base[c * stride];
         } else if (g.periodic) {
-            v[k] = (c < 0) ? base[(c + n) * stride] - seam : base[(c - n) * stride] + seam;
+            const int cw = (c < 0) ? c + n : c - n;
+            v[k] = !ZM_IDX_OK(cw, n) ? 0.0 : (c < 0) ? base[cw * stride] - seam : base[cw * stride] + seam;
         } else {
-            v[k] = (c < 0) ? 2.0 * base[0] - base[(-c) * stride]
-                           : 2.0 * base[(n - 1) * stride] - base[(2 * (n - 1) - c) * stride];
+            const int e = (c < 0) ? 0 : n - 1, m = (c < 0) ? -c : 2 * (n - 1) - c;
+            v[k] = ZM_IDX_OK(m, n) ? 2.0 * base[e * stride] - base[m * stride] : 0.0;
         }
     }
 }
@@ -60,6 +61,7 @@ __device__ __forceinline__ void geometry_point(const Geom &g, const Tiling &t, i
                                                unsigned int *gmax, double *__restrict__ q,
                                                double *__restrict__ nrm)
 {
+    if (!ZM_IDX_OK(p, g.N)) return;
     const int i = p / g.n2, j = p - (p / g.n2) * g.n2;
     const double *z = y, *w = y + 3 * (size_t)g.N;
     const double i12a = g.i12a, i12b = g.i12b;
@@ -101,6 +103,7 @@ __device__ __forceinline__ void geometry_point(const Geom &g, const Tiling &t, i
     const int ti = i / t.tp1, tj = j / t.tp2;
     const size_t tile = (size_t)ti * t.nt2 + tj;
     const int slot = (i - ti * t.tp1) * t.tp2 + (j - tj * t.tp2);
+    if (!ZM_IDX_OK(tile, t.ntiles) || !ZM_IDX_OK(slot, t.ts)) return;
     if (kKind == kGeoFp32c) {
         // near record: hi/lo position and strength
         float *r = static_cast<float *>(src) + tile * kRec32 * t.ts + slot;
@@ -118,6 +121,7 @@ __device__ __forceinline__ void geometry_point(const Geom &g, const Tiling &t, i
         // of the mesh), |s|^2 + delta^2, strength and s x strength
         const int h1 = min(t.tp1, g.n1 - ti * t.tp1), h2 = min(t.tp2, g.n2 - tj * t.tp2);
         const size_t pc = (size_t)(ti * t.tp1 + h1 / 2) * g.n2 + (tj * t.tp2 + h2 / 2);
+        if (!ZM_IDX_OK(pc, g.N)) return;
         float cf[3], sf[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -163,6 +167,7 @@ __device__ __forceinline__ void vorticity_point(const Geom &g, int p, const doub
                                                 const double *y0, double *yout,
                                                 double *__restrict__ wdot)
 {
+    if (!ZM_IDX_OK(p, g.N)) return;
     const int i = p / g.n2, j = p - (p / g.n2) * g.n2;
     const size_t N = g.N;
     double v[5];

@@ -66,7 +66,8 @@ VP = ctypes.c_void_p
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """libzm.so, or the checked build libzm_checked.so when ZM_LIB=checked."""
+    return _build.LIB_CHECKED if os.environ.get("ZM_LIB") == "checked" else _build.LIB
 
 
 def load():
@@ -98,6 +99,9 @@ def load():
             "zm_measure_peak": (I, [I, ctypes.POINTER(D)]),
             "zm_wait_selftest": (I, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(D)]),
             "zm_wait_poll_limit": (ctypes.c_int64, []),
+            "zm_checked_build": (I, []),
+            "zm_bounds_status": (I, [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
             "zm_br_velocity_noalloc": (I, [ctypes.c_int32, VP, VP, D, VP, VP, VP]),
             "zm_batch_create": (I, [ctypes.c_int32, ctypes.POINTER(zm_mesh), ctypes.POINTER(D), D, D,
                                     ctypes.POINTER(D), ctypes.POINTER(VP)]),
@@ -335,6 +339,17 @@ def zm_autotune(h, cache_path=None):
     p = cache_path.encode() if cache_path else None
     _check(load().zm_autotune(h, p, ctypes.byref(c)))
     return c.value
+
+
+def zm_checked_build():
+    return bool(load().zm_checked_build())
+
+
+def zm_bounds_status(clear=True):
+    """Index violations counted by the checked build: (hits, first index, source line)."""
+    h, f, ln = ctypes.c_uint32(), ctypes.c_int64(), ctypes.c_int32()
+    _check(load().zm_bounds_status(ctypes.byref(h), ctypes.byref(f), ctypes.byref(ln), int(bool(clear))))
+    return h.value, f.value, ln.value
 
 
 def zm_autotune_tiles(h, cache_path=None):

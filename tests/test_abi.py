@@ -38,6 +38,11 @@ def test_library_exports_every_declared_symbol():
     lib.zm_error_string.restype = ctypes.c_char_p
     assert lib.zm_error_string(0) == b"ok"
     assert lib.zm_error_string(-5) == b"unsupported configuration"
+    # the checked build (same sources, ZM_CHECKS=1) exports the same entry points and says so
+    chk = ctypes.CDLL(build.LIB_CHECKED)
+    missing = [n for n in declared_functions() if not hasattr(chk, n)]
+    assert not missing, missing
+    assert lib.zm_checked_build() == 0 and chk.zm_checked_build() == 1
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

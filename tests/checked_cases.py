@@ -27,17 +27,13 @@ def main(out_path):
     zm.zm_bounds_status(clear=True)
     res = {}
 
-    def model_case(name, n1, n2, periodic, order, fp32c=False, df64=False, mu=0.0, steps=2, cutoff=0.0,
-                   tiles=None):
+    def model_case(name, n1, n2, periodic, order, fp32c=False, df64=False, mu=0.0, steps=2, cutoff=0.0):
         z, w = inputs.random_state(n1, n2, seed=n1 + 7 * n2, periodic=periodic)
         delta = 0.1 / max(n1, n2)
         m = zm.ZModel(n1, n2, periodic=periodic, atwood=0.6, g=1.2, mu=mu, delta=delta, order=order,
                       fp32c=fp32c, df64=df64)
         if cutoff:
             zm.zm_set_cutoff(m.h, cutoff)
-        if tiles:
-            tl, ch = zm.zm_autotune_tiles(m.h)
-            res[name + "_tiles"] = np.array(tl + (ch,))
         u, wd = m.velocity(z, w)
         m.set_state(z, w)
         m.step(1e-3, steps)
@@ -49,7 +45,7 @@ def main(out_path):
     model_case("fp64_free", 32, 24, False, H)
     model_case("fp64_per", 40, 48, True, H, mu=0.01)
     model_case("fp32c", 64, 64, True, H, fp32c=True)
-    model_case("fp32c_aniso", 32, 128, True, H, fp32c=True, tiles=True)
+    model_case("fp32c_aniso", 32, 128, True, H, fp32c=True)
     model_case("fp32c_cut", 64, 64, True, H, fp32c=True, cutoff=0.2)
     model_case("low_p2", 64, 32, True, LO, mu=0.01)
     model_case("low_mix", 24, 40, True, LO)
@@ -68,6 +64,14 @@ def main(out_path):
         zm.zm_batch_set_state(h, k, *inputs.random_state(a, b, seed=k, periodic=p))
     zm.zm_batch_step(h, 1e-3, 2)
     zm.zm_batch_sync(h)
+    # every other tile shape, one evaluation each (timing-based tuning would differ between runs)
+    for tp1, tp2 in ((8, 32), (32, 8), (4, 64), (64, 4)):
+        zm.zm_batch_set_tile_shape(h, tp1, tp2)
+        zm.zm_batch_velocity(h)
+        for k, (a, b, _) in enumerate(specs):
+            ub = np.empty((3, a * b))
+            zm.zm_batch_get_velocity(h, k, ub, None)
+            res[f"batch{k}_u_{tp1}x{tp2}"] = ub
     for k, (a, b, _) in enumerate(specs):
         zb, wb = np.empty((3, a * b)), np.empty((2, a * b))
         zm.zm_batch_get_state(h, k, zb, wb)

@@ -40,9 +40,12 @@
 namespace zm {
 namespace {
 
-constexpr int kT = 64;    // threads per CTA
-constexpr int kR = 4;     // targets per thread: one 16 x 16 target tile per CTA
-constexpr int kTs = 256;  // sources per tile
+#ifndef ZM_BR32_R
+#define ZM_BR32_R 4
+#endif
+constexpr int kTs = 256;        // sources per tile (and targets per target tile)
+constexpr int kR = ZM_BR32_R;   // targets per thread
+constexpr int kT = kTs / kR;    // threads per CTA: one target tile per CTA
 constexpr float kFarFactor = 1.25f;
 
 // compile-time tuning: unroll of the far loop over source pairs, and the minimum resident CTAs

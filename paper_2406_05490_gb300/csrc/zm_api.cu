@@ -216,7 +216,7 @@ void zm_destroy(zm_ctx *c)
         c->y0 = c->ya = c->yb = c->u = c->phi = c->q = nullptr;
     }
     void *bufs[] = {c->y0, c->ya, c->yb, c->u, c->phi, c->q, c->nrm, c->src, c->part,
-                    c->fa, c->fb, c->tw1, c->tw2, c->twl1, c->twl2, c->err, c->flag};
+                    c->fa, c->fb, c->tw1, c->tw2, c->twl1, c->twl2, c->twh, c->err, c->flag};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (prev >= 0) cudaSetDevice(prev);

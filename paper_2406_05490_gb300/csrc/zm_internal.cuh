@@ -148,6 +148,7 @@ struct zm_ctx {
     // low order: FFT workspace (complex doubles) and twiddles: tw1, tw2 for the power-of-two
     // factor M of each side, twl1, twl2 for the whole side L = R M when R > 1 (else null)
     double2 *fa, *fb, *tw1, *tw2, *twl1, *twl2;
+    double2 *twh;  // double word, both sides powers of two: half table of W_{n2/2} (else null)
 
     int *err;   // device status word (zm::kErr*)
     int *flag;  // device scratch flag (finite check)

@@ -277,6 +277,104 @@ __global__ void __launch_bounds__(threads_for(L), minb_for(L))
     }
 }
 
+// ---- Hermitian inverse (both sides powers of two) ------------------------------------------------
+// The spectrum of the real field s is Hermitian, S(-k) = conj S(k), and with Q = (m1 - i m2) P
+// (P the spectrum of w1 + i w2) it is S(k) = (Q(k) + conj Q(-k)) / 2, so only the columns
+// k2 = 0 .. n2/2 need the inverse along alpha1, and each row then holds a Hermitian sequence
+// whose real inverse of length n2 is one complex inverse of length n2/2 (the even and odd
+// samples as real and imaginary parts).  The Nyquist column k2 = n2/2 has a zero multiplier.
+// This halves the inverse transforms against the full complex inverse of the passes above.
+//
+// Pass B_h: a CTA takes rows/2 column pairs (q, n2 - q), q = q0 .. q0 + rows/2 - 1, the pair
+// q = 0 being (0, n2/2): columns q in local rows 0 .. rows/2 - 1, their mirrors in the rest.  It
+// transforms all of them forward, forms 2 S(., q) = Q(., q) + conj Q(-., mirror) in the local
+// row of q, transforms those rows back and writes G(i, q) = 2 x (the alpha1 inverse of S) to
+// out[i][q], n2/2 columns.
+__device__ __forceinline__ C2 conj2(C2 a) { return C2{a.h ^ kSign1, a.l ^ kSign1}; }
+
+template <int L>
+__global__ void __launch_bounds__(threads_for(L), minb_for(L))
+    pass_b_h(int n2, int lr, Dc invL1, Dc invL2, const ulonglong2 *__restrict__ in,
+             const ulonglong2 *__restrict__ tw1, ulonglong2 *__restrict__ out)
+{
+    extern __shared__ ulonglong2 sx[];
+    constexpr int n1 = 1 << L;
+    const int rows = 1 << lr, hr = rows >> 1;
+    const int q0 = blockIdx.x * hr;
+    if (!ZM_IDX_OK(q0 + hr - 1, n2 / 2)) return;  // checked build: the CTA's pairs exist
+    auto col = [&](int row) {
+        const int q = q0 + (row < hr ? row : row - hr);
+        return row < hr ? q : (q == 0 ? n2 / 2 : n2 - q);
+    };
+    auto ldg = [&](int row, int i) { return ld2(in[(size_t)col(row) * n1 + i]); };
+    dif_seq<L, 0, nc_of(L) - 1>(sx, tw1, rows, -1, ldg);
+    // 2 S at frequencies k1 and -k1 of column q from Q of column q and of its mirror
+    for (int e = threadIdx.x; e < hr * (n1 / 2 + 1); e += blockDim.x) {
+        const int t = e / (n1 / 2 + 1), k1 = e - t * (n1 / 2 + 1);
+        const int km = (n1 - k1) & (n1 - 1);
+        const int q = q0 + t, cm = (q == 0) ? 0 : n2 - q;  // the mirror column of q
+        const int ra = t << L, rm = ((q == 0 ? t : hr + t) << L);
+        const int pk = bitrev(k1, L), pkm = bitrev(km, L);
+        const C2 qa = cmul2(ld2(sx[phys(ra + pk)]), riesz_mult(k1, q, n1, n2, invL1, invL2));
+        const C2 qam = cmul2(ld2(sx[phys(ra + pkm)]), riesz_mult(km, q, n1, n2, invL1, invL2));
+        const C2 qb = cmul2(ld2(sx[phys(rm + pk)]), riesz_mult(k1, cm, n1, n2, invL1, invL2));
+        const C2 qbm = cmul2(ld2(sx[phys(rm + pkm)]), riesz_mult(km, cm, n1, n2, invL1, invL2));
+        const C2 s0 = cadd2(qa, conj2(qbm)), s1 = cadd2(qam, conj2(qb));
+        sx[phys(ra + pk)] = st2(s0);
+        if (km != k1) sx[phys(ra + pkm)] = st2(s1);
+    }
+    __syncthreads();
+    dit_seq<L, nc_of(L) - 1>(sx, tw1, hr, +1);
+    for (int e = threadIdx.x; e < (hr << L); e += blockDim.x) {
+        const int i = e >> (lr - 1), t = e & (hr - 1);
+        out[(size_t)i * (n2 / 2) + q0 + t] = sx[phys((t << L) + i)];
+    }
+}
+
+// Pass C_h: rows i of G (length M = n2/2 = 2^L); the real inverse of length n2 as the complex
+// inverse of Z[k] = (G[k] + conj G[M - k]) + i W_n2^(-k) (G[k] - conj G[M - k]) (G[M] = 0), whose
+// output m holds s[2m] + i s[2m + 1]; then u = -s/2 N and Phi = q + |u|^2 / 2.  twn: half table
+// of W_n2, twm: of W_M.  scale = -1 / (4 n1 n2) (the 1/2 of S and of u, the 1/(n1 n2) of the
+// inverse).
+template <int L>
+__global__ void __launch_bounds__(threads_for(L), minb_for(L))
+    pass_c_h(int n1, int lr, Dc scale, const ulonglong2 *__restrict__ in, const ulonglong2 *__restrict__ twm,
+             const ulonglong2 *__restrict__ twn, const float2 *__restrict__ nrm, const float2 *__restrict__ q,
+             float2 *__restrict__ u, float2 *__restrict__ phi)
+{
+    extern __shared__ ulonglong2 sx[];
+    constexpr int M = 1 << L, n2 = 2 * M;
+    const int rows = 1 << lr;
+    const int i0 = blockIdx.x * rows;
+    if (!ZM_IDX_OK(i0 + rows - 1, n1)) return;  // checked build: the CTA's rows exist
+    const size_t N = (size_t)n1 * n2;
+    const ulonglong2 *src = in + (size_t)i0 * M;
+    auto ldz = [&](int row, int k) {
+        const C2 g = ld2(src[row * M + k]);
+        const C2 gm = k ? conj2(ld2(src[row * M + M - k])) : C2{0ull, 0ull};
+        const C2 a = cadd2(g, gm), b = csub2(g, gm);
+        return cadd2(a, cmul_i2(k ? cmul2(b, tw_get(twn, k, M, +1)) : b, +1));
+    };
+    dif_seq<L, 0, nc_of(L) - 1>(sx, twm, rows, +1, ldz);
+    const df sc = dc(scale);
+    for (int e = threadIdx.x; e < rows * M; e += blockDim.x) {
+        const int r = e >> L, m = e & (M - 1);
+        const C2 z = ld2(sx[phys((r << L) + bitrev(m, L))]);
+        const size_t p0 = (size_t)(i0 + r) * n2 + 2 * m;
+        const df s2[2] = {mul(df{lane0(z.h), lane0(z.l)}, sc), mul(df{lane1(z.h), lane1(z.l)}, sc)};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const size_t p = p0 + h;
+            const df ux = mul(s2[h], ldf(nrm, p)), uy = mul(s2[h], ldf(nrm, N + p)), uz = mul(s2[h], ldf(nrm, 2 * N + p));
+            u[p] = to_f2(ux);
+            u[N + p] = to_f2(uy);
+            u[2 * N + p] = to_f2(uz);
+            const df k2 = add(add(sqr(ux), sqr(uy)), sqr(uz));
+            phi[p] = to_f2(add(ldf(q, p), scale2(k2, 0.5f)));
+        }
+    }
+}
+
 // twiddle table entry k < L/2: {cos.hi, sin.hi, cos.lo, sin.lo} of -2 pi k / L
 __global__ void twiddle_df_kernel(int L, float4 *tw)
 {
@@ -396,6 +494,23 @@ struct FftLaunch {
         pass_b_df<L><<<n2 >> lr, threads_for(L), smem, s>>>(n2, lr, invL1, invL2, in, tw1, out);
         return cuda_check(cudaGetLastError(), "double-word FFT pass B launch");
     }
+    static int b_h(int n2, int lr, size_t smem, cudaStream_t s, Dc invL1, Dc invL2, const ulonglong2 *in,
+                   const ulonglong2 *tw1, ulonglong2 *out)
+    {
+        int rc = smem_attr((const void *)pass_b_h<L>, smem);
+        if (rc) return rc;
+        pass_b_h<L><<<n2 >> lr, threads_for(L), smem, s>>>(n2, lr, invL1, invL2, in, tw1, out);
+        return cuda_check(cudaGetLastError(), "double-word FFT pass B (Hermitian) launch");
+    }
+    static int c_h(int n1, int lr, size_t smem, cudaStream_t s, Dc scale, const ulonglong2 *in,
+                   const ulonglong2 *twm, const ulonglong2 *twn, const float2 *nrm, const float2 *q, float2 *u,
+                   float2 *phi)
+    {
+        int rc = smem_attr((const void *)pass_c_h<L>, smem);
+        if (rc) return rc;
+        pass_c_h<L><<<n1 >> lr, threads_for(L), smem, s>>>(n1, lr, scale, in, twm, twn, nrm, q, u, phi);
+        return cuda_check(cudaGetLastError(), "double-word FFT pass C (Hermitian) launch");
+    }
     static int c(int n1, int lr, size_t smem, cudaStream_t s, Dc scale, const ulonglong2 *in,
                  const ulonglong2 *tw2, const float2 *nrm, const float2 *q, float2 *u, float2 *phi)
     {
@@ -418,6 +533,12 @@ DfSide df_side(int L)
 }
 
 }  // namespace
+
+// Meshes whose double-word Riesz pass uses the Hermitian inverse: both sides powers of two,
+// n2 >= 16 (the half-length row transform has at least 8 values) and n1 <= 2048 (pass B_h holds
+// a column pair per CTA; with columns of 4096 that is 139 KB of shared memory and one CTA per
+// SM, and measured at 4096^2 it gained nothing: 724 us against the full inverse's pass B).
+bool herm_sides(int n1, int n2) { return pow2_side(n1) && pow2_side(n2) && n2 >= 16 && n1 <= 2048; }
 
 bool df_side_ok(int L)
 {
@@ -453,6 +574,13 @@ int df_setup(zm_ctx *c)
     twiddle_df_kernel<<<(m2 / 2 + 255) / 256, 256>>>(m2, reinterpret_cast<float4 *>(c->tw2));
     if (c->twl1) twiddle_df_kernel<<<(g.n1 / 2 + 255) / 256, 256>>>(g.n1, reinterpret_cast<float4 *>(c->twl1));
     if (c->twl2) twiddle_df_kernel<<<(g.n2 / 2 + 255) / 256, 256>>>(g.n2, reinterpret_cast<float4 *>(c->twl2));
+    if (herm_sides(g.n1, g.n2)) {  // the Hermitian inverse's half-length row transform
+        if (cudaMalloc(&c->twh, (g.n2 / 4) * sizeof(double2)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ZM_ERR_NOMEM, "df_setup: device allocation failed");
+        }
+        twiddle_df_kernel<<<(g.n2 / 4 + 255) / 256, 256>>>(g.n2 / 2, reinterpret_cast<float4 *>(c->twh));
+    }
     int rc = ZM_OK;
     if (!rc) rc = cuda_check(cudaGetLastError(), "df twiddle kernel");
     return rc;
@@ -493,19 +621,34 @@ int df_derivative(zm_ctx *c, const double *y)
         return s2.R > 1 ? df_mix_pass_a(A, G.n1, s2.R, ra, sa, c->stream, w, U2(c->tw2), U2(c->twl2), U2(c->fa))
                         : FftLaunch<A>::a(G.n1, ra, sa, c->stream, w, U2(c->tw2), U2(c->fa));
     });
-    if (!rc) rc = with_log2(s1.A, [&](auto lc) {
-        constexpr int A = decltype(lc)::value;
-        return s1.R > 1 ? df_mix_pass_b(A, G.n2, s1.R, rb, sb, c->stream, 1.0 / G.L1, 1.0 / G.L2, U2(c->fa),
-                                        U2(c->tw1), U2(c->twl1), U2(c->fb))
-                        : FftLaunch<A>::b(G.n2, rb, sb, c->stream, iL1, iL2, U2(c->fa), U2(c->tw1), U2(c->fb));
-    });
-    if (!rc) rc = with_log2(s2.A, [&](auto lc) {
-        constexpr int A = decltype(lc)::value;
-        return s2.R > 1 ? df_mix_pass_c(A, G.n1, s2.R, ra, sa, c->stream, scale, U2(c->fb), U2(c->tw2),
-                                        U2(c->twl2), F2(c->nrm), F2(c->q), F2(c->u), F2(c->phi))
-                        : FftLaunch<A>::c(G.n1, ra, sa, c->stream, split(scale), U2(c->fb), U2(c->tw2), F2(c->nrm),
-                                          F2(c->q), F2(c->u), F2(c->phi));
-    });
+    if (c->twh) {  // Hermitian inverse: half the columns back along alpha1, then real rows
+        const int rbh = std::max(1, lrows_for(s1.A, G.n2)), rch = lrows_for(s2.A - 1, G.n1);  // rows >= 2
+        const size_t sbh = (size_t)phys_host(G.n1 << rbh) * sizeof(ulonglong2);
+        const size_t sch = (size_t)phys_host((G.n2 / 2) << rch) * sizeof(ulonglong2);
+        if (!rc) rc = with_log2(s1.A, [&](auto lc) {
+            return FftLaunch<decltype(lc)::value>::b_h(G.n2, rbh, sbh, c->stream, iL1, iL2, U2(c->fa), U2(c->tw1),
+                                                       U2(c->fb));
+        });
+        if (!rc) rc = with_log2(s2.A - 1, [&](auto lc) {
+            return FftLaunch<decltype(lc)::value>::c_h(G.n1, rch, sch, c->stream, split(scale / 2), U2(c->fb),
+                                                       U2(c->twh), U2(c->tw2), F2(c->nrm), F2(c->q), F2(c->u),
+                                                       F2(c->phi));
+        });
+    } else {
+        if (!rc) rc = with_log2(s1.A, [&](auto lc) {
+            constexpr int A = decltype(lc)::value;
+            return s1.R > 1 ? df_mix_pass_b(A, G.n2, s1.R, rb, sb, c->stream, 1.0 / G.L1, 1.0 / G.L2, U2(c->fa),
+                                            U2(c->tw1), U2(c->twl1), U2(c->fb))
+                            : FftLaunch<A>::b(G.n2, rb, sb, c->stream, iL1, iL2, U2(c->fa), U2(c->tw1), U2(c->fb));
+        });
+        if (!rc) rc = with_log2(s2.A, [&](auto lc) {
+            constexpr int A = decltype(lc)::value;
+            return s2.R > 1 ? df_mix_pass_c(A, G.n1, s2.R, ra, sa, c->stream, scale, U2(c->fb), U2(c->tw2),
+                                            U2(c->twl2), F2(c->nrm), F2(c->q), F2(c->u), F2(c->phi))
+                            : FftLaunch<A>::c(G.n1, ra, sa, c->stream, split(scale), U2(c->fb), U2(c->tw2),
+                                              F2(c->nrm), F2(c->q), F2(c->u), F2(c->phi));
+        });
+    }
     prof_end(c, ZM_K_FFT, ev);
     c->prof.acc.launches[ZM_K_FFT] += 2;  // three kernels per Riesz evaluation
     if (rc) return rc;

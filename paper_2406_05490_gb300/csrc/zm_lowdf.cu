@@ -538,7 +538,13 @@ DfSide df_side(int L)
 // n2 >= 16 (the half-length row transform has at least 8 values) and n1 <= 2048 (pass B_h holds
 // a column pair per CTA; with columns of 4096 that is 139 KB of shared memory and one CTA per
 // SM, and measured at 4096^2 it gained nothing: 724 us against the full inverse's pass B).
-bool herm_sides(int n1, int n2) { return pow2_side(n1) && pow2_side(n2) && n2 >= 16 && n1 <= 2048; }
+#ifndef ZM_DF_HERM
+#define ZM_DF_HERM 1  // 0: the full complex inverse everywhere
+#endif
+bool herm_sides(int n1, int n2)
+{
+    return ZM_DF_HERM && pow2_side(n1) && pow2_side(n2) && n2 >= 16 && n1 <= 2048;
+}
 
 bool df_side_ok(int L)
 {

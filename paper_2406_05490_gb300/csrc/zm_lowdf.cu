@@ -535,15 +535,18 @@ DfSide df_side(int L)
 }  // namespace
 
 // Meshes whose double-word Riesz pass uses the Hermitian inverse: both sides powers of two,
-// n2 >= 16 (the half-length row transform has at least 8 values) and n1 <= 2048 (pass B_h holds
-// a column pair per CTA; with columns of 4096 that is 139 KB of shared memory and one CTA per
-// SM, and measured at 4096^2 it gained nothing: 724 us against the full inverse's pass B).
+// n2 >= 16 (the half-length row transform has at least 8 values) and columns of 2048.  Measured
+// on GB300 against the full inverse (FFT ms per evaluation): 512^2 0.0634 vs 0.0587, 1024^2
+// 0.0961 vs 0.0969, 2048^2 0.3098 vs 0.3311; at 4096^2 the column pair of pass B_h needs 139 KB
+// of shared memory (one CTA per SM) and gained nothing.  Below 2048 the unfused middle of pass
+// B_h (the fused last-forward / multiplier / first-inverse group of pass B is lost) outweighs
+// the halved inverse.
 #ifndef ZM_DF_HERM
 #define ZM_DF_HERM 1  // 0: the full complex inverse everywhere
 #endif
 bool herm_sides(int n1, int n2)
 {
-    return ZM_DF_HERM && pow2_side(n1) && pow2_side(n2) && n2 >= 16 && n1 <= 2048;
+    return ZM_DF_HERM && pow2_side(n1) && pow2_side(n2) && n2 >= 16 && n1 == 2048;
 }
 
 bool df_side_ok(int L)

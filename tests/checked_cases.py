@@ -55,6 +55,7 @@ def main(out_path):
     model_case("df_p2", 64, 32, True, LO, df64=True, mu=0.01)
     model_case("df_mix", 24, 40, True, LO, df64=True)
     model_case("df_mix19", 608, 152, True, LO, df64=True, steps=1)
+    model_case("df_herm", 2048, 32, True, LO, df64=True, steps=1)
 
     # a ragged batch
     specs = [(37, 53, False), (64, 64, True), (5, 9, False), (48, 40, True)]

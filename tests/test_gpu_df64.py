@@ -52,7 +52,9 @@ def zm():
                                       # sides R 2^A: every odd factor R = 3 .. 19 once, A = 3 .. 11
                                       (24, 40, 0.0), (56, 72, 0.01), (88, 104, 0.0), (120, 136, 0.0),
                                       (152, 16, 0.0), (96, 320, 0.003), (608, 152, 0.0), (6144, 8, 0.0),
-                                      (8, 6144, 0.0)])
+                                      (8, 6144, 0.0),
+                                      # columns of 2048: the Hermitian inverse (pass B_h / C_h)
+                                      (2048, 16, 0.0), (2048, 64, 0.01)])
 def test_df64_velocity_parity(zm, n1, n2, mu):
     z, w = inputs.random_state(n1, n2, seed=n1 + 2 * n2)
     m = oracle.Mesh(n1, n2, periodic=True)

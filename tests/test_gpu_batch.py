@@ -222,3 +222,32 @@ def test_tile_autotune_on_an_anisotropic_mesh(zm, tmp_path):
     print(f"anisotropic 64x256: rel L2 u={rel(u, u_ref):.3e} wdot={rel(wd, wd_ref):.3e} (bound {tol_wd:.2e})")
     assert rel(u, u_ref) <= TOL32 and rel(wd, wd_ref) <= tol_wd
     torch.cuda.synchronize()
+
+
+def test_bench_batch_of_64_sampled(zm):
+    """The batched configuration itself: 64 periodic interfaces, sides log-uniform in [64, 384]
+    (seed 0), 4 modes, A ~ U[0.2, 0.8], FP32C, one graph-replayed RK3 step on the whole batch;
+    eight seeded interfaces of side <= 100 (so that the serial oracle finishes in seconds)
+    against the oracle's step, on the state and on the displacement z - z0 (w starts at 0,
+    so the first stage moves nothing and the step is carried by the later stages)."""
+    insts = inputs.ragged_batch(count=64, lo=64, hi=384, n_modes=4, seed=0)
+    delta = [0.1 / r.n for r in insts]
+    h = zm.zm_batch_create([(r.n, r.n, 1.0, 1.0, True) for r in insts], [r.atwood for r in insts], g=1.0,
+                           delta=delta)
+    for k, r in enumerate(insts):
+        zm.zm_batch_set_state(h, k, r.z, r.w)
+    zm.zm_batch_step(h, 1e-3, 1)
+    zm.zm_batch_sync(h)
+    small = [k for k, r in enumerate(insts) if r.n <= 100]
+    pick = sorted(np.random.default_rng(1).choice(small, size=min(8, len(small)), replace=False).tolist())
+    assert len(pick) == 8
+    for k in pick:
+        r = insts[k]
+        N = r.n * r.n
+        z1, w1 = np.empty((3, N)), np.empty((2, N))
+        zm.zm_batch_get_state(h, k, z1, w1)
+        zr, wr = oracle.run(oracle.Mesh(r.n, periodic=True), r.z, r.w, r.atwood, 1.0, 0.0, delta[k], 1e-3, 1)
+        ez, ew, dz = rel(z1, zr), rel(w1, wr), rel(z1 - r.z, zr - r.z)
+        print(f"batch of 64, interface {k} ({r.n}^2): rel L2 z={ez:.3e} w={ew:.3e} (z - z0)={dz:.3e}")
+        assert ez <= TOL32 and ew <= TOL32 and dz <= 1e-5
+    zm.zm_batch_destroy(h)

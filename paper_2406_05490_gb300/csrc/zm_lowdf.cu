@@ -508,7 +508,10 @@ struct FftLaunch {
     {
         int rc = smem_attr((const void *)pass_c_h<L>, smem);
         if (rc) return rc;
-        pass_c_h<L><<<n1 >> lr, threads_for(L), smem, s>>>(n1, lr, scale, in, twm, twn, nrm, q, u, phi);
+        // one group of 16 values per thread over the CTA's rows (fewer threads than threads_for(L)
+        // when the rows hold fewer than kFftElems values)
+        const int threads = std::max(32, std::min(threads_for(L), ((1 << L) << lr) / 16));
+        pass_c_h<L><<<n1 >> lr, threads, smem, s>>>(n1, lr, scale, in, twm, twn, nrm, q, u, phi);
         return cuda_check(cudaGetLastError(), "double-word FFT pass C (Hermitian) launch");
     }
     static int c(int n1, int lr, size_t smem, cudaStream_t s, Dc scale, const ulonglong2 *in,
@@ -631,7 +634,13 @@ int df_derivative(zm_ctx *c, const double *y)
                         : FftLaunch<A>::a(G.n1, ra, sa, c->stream, w, U2(c->tw2), U2(c->fa));
     });
     if (c->twh) {  // Hermitian inverse: half the columns back along alpha1, then real rows
-        const int rbh = std::max(1, lrows_for(s1.A, G.n2)), rch = lrows_for(s2.A - 1, G.n1);  // rows >= 2
+#ifndef ZM_DF_CH_ROWS_SHIFT
+#define ZM_DF_CH_ROWS_SHIFT 1
+#endif
+        // pass C_h rows per CTA: half the usual budget (2048 values), so that the half-length rows
+        // make twice as many, smaller CTAs (1024 rather than 512 at 2048^2: 1.3 waves were left)
+        const int rbh = std::max(1, lrows_for(s1.A, G.n2));  // a column pair: rows >= 2
+        const int rch = std::max(0, lrows_for(s2.A - 1, G.n1) - ZM_DF_CH_ROWS_SHIFT);
         const size_t sbh = (size_t)phys_host(G.n1 << rbh) * sizeof(ulonglong2);
         const size_t sch = (size_t)phys_host((G.n2 / 2) << rch) * sizeof(ulonglong2);
         if (!rc) rc = with_log2(s1.A, [&](auto lc) {

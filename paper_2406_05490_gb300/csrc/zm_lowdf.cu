@@ -440,6 +440,28 @@ int lrows_for(int l, int avail)
     return r;
 }
 
+// Fewer rows per CTA (down to one) while the pass would have fewer than `floor` CTAs: small
+// meshes then fill the GPU with more, smaller CTAs (pass_threads gives each one thread per group
+// of 16 values).  Measured A/B on GB300 (FFT ms per evaluation; floors 0 / 304 / 456 / 608):
+// 512^2 0.0587 / 0.0444 / 0.0449 / 0.0446, 1024^2 0.0969 / 0.0972 / 0.0976 / 0.1015; at 2048^2
+// only the Hermitian pass C gains (floor 608: 512 -> 1024 CTAs, 0.310 -> 0.302 ms).
+#ifndef ZM_DF_MINGRID
+#define ZM_DF_MINGRID 304  // two CTAs per SM of the 152
+#endif
+#ifndef ZM_DF_MINGRID_CH
+#define ZM_DF_MINGRID_CH 608  // the Hermitian pass C: four per SM
+#endif
+int lrows_grid(int l, int avail, int floor = ZM_DF_MINGRID)
+{
+    int r = lrows_for(l, avail);
+    while (r > 0 && (avail >> r) < floor) --r;
+    return r;
+}
+
+// Threads per CTA of a pass over 2^lr rows of length 2^L: one per group of 16 values, at most
+// threads_for(L) (the launch bound).
+int pass_threads(int L, int lr) { return std::max(32, std::min(threads_for(L), ((1 << L) << lr) / 16)); }
+
 // The same for rows of length L = R 2^A (not a power of two): rows * L <= kFftElems.
 int lrows_mix(int L, int avail)
 {
@@ -483,7 +505,7 @@ struct FftLaunch {
     {
         int rc = smem_attr((const void *)pass_a_df<L>, smem);
         if (rc) return rc;
-        pass_a_df<L><<<n1 >> lr, threads_for(L), smem, s>>>(n1, lr, w, tw2, out);
+        pass_a_df<L><<<n1 >> lr, pass_threads(L, lr), smem, s>>>(n1, lr, w, tw2, out);
         return cuda_check(cudaGetLastError(), "double-word FFT pass A launch");
     }
     static int b(int n2, int lr, size_t smem, cudaStream_t s, Dc invL1, Dc invL2, const ulonglong2 *in,
@@ -491,7 +513,7 @@ struct FftLaunch {
     {
         int rc = smem_attr((const void *)pass_b_df<L>, smem);
         if (rc) return rc;
-        pass_b_df<L><<<n2 >> lr, threads_for(L), smem, s>>>(n2, lr, invL1, invL2, in, tw1, out);
+        pass_b_df<L><<<n2 >> lr, pass_threads(L, lr), smem, s>>>(n2, lr, invL1, invL2, in, tw1, out);
         return cuda_check(cudaGetLastError(), "double-word FFT pass B launch");
     }
     static int b_h(int n2, int lr, size_t smem, cudaStream_t s, Dc invL1, Dc invL2, const ulonglong2 *in,
@@ -499,7 +521,7 @@ struct FftLaunch {
     {
         int rc = smem_attr((const void *)pass_b_h<L>, smem);
         if (rc) return rc;
-        pass_b_h<L><<<n2 >> lr, threads_for(L), smem, s>>>(n2, lr, invL1, invL2, in, tw1, out);
+        pass_b_h<L><<<n2 >> lr, pass_threads(L, lr), smem, s>>>(n2, lr, invL1, invL2, in, tw1, out);
         return cuda_check(cudaGetLastError(), "double-word FFT pass B (Hermitian) launch");
     }
     static int c_h(int n1, int lr, size_t smem, cudaStream_t s, Dc scale, const ulonglong2 *in,
@@ -508,10 +530,7 @@ struct FftLaunch {
     {
         int rc = smem_attr((const void *)pass_c_h<L>, smem);
         if (rc) return rc;
-        // one group of 16 values per thread over the CTA's rows (fewer threads than threads_for(L)
-        // when the rows hold fewer than kFftElems values)
-        const int threads = std::max(32, std::min(threads_for(L), ((1 << L) << lr) / 16));
-        pass_c_h<L><<<n1 >> lr, threads, smem, s>>>(n1, lr, scale, in, twm, twn, nrm, q, u, phi);
+        pass_c_h<L><<<n1 >> lr, pass_threads(L, lr), smem, s>>>(n1, lr, scale, in, twm, twn, nrm, q, u, phi);
         return cuda_check(cudaGetLastError(), "double-word FFT pass C (Hermitian) launch");
     }
     static int c(int n1, int lr, size_t smem, cudaStream_t s, Dc scale, const ulonglong2 *in,
@@ -519,7 +538,7 @@ struct FftLaunch {
     {
         int rc = smem_attr((const void *)pass_c_df<L>, smem);
         if (rc) return rc;
-        pass_c_df<L><<<n1 >> lr, threads_for(L), smem, s>>>(n1, lr, scale, in, tw2, nrm, q, u, phi);
+        pass_c_df<L><<<n1 >> lr, pass_threads(L, lr), smem, s>>>(n1, lr, scale, in, tw2, nrm, q, u, phi);
         return cuda_check(cudaGetLastError(), "double-word FFT pass C launch");
     }
 };
@@ -618,8 +637,8 @@ int df_derivative(zm_ctx *c, const double *y)
     const DfSide s1 = df_side(G.n1), s2 = df_side(G.n2);
     if ((s1.R > 1 && !c->twl1) || (s2.R > 1 && !c->twl2))
         return set_error(ZM_ERR_INVALID, "double-word derivative: missing twiddle table");
-    const int ra = s2.R > 1 ? lrows_mix(G.n2, G.n1) : lrows_for(s2.A, G.n1);
-    const int rb = s1.R > 1 ? lrows_mix(G.n1, G.n2) : lrows_for(s1.A, G.n2);
+    const int ra = s2.R > 1 ? lrows_mix(G.n2, G.n1) : lrows_grid(s2.A, G.n1);
+    const int rb = s1.R > 1 ? lrows_mix(G.n1, G.n2) : lrows_grid(s1.A, G.n2);
     if (G.n1 % (1 << ra) || G.n2 % (1 << rb))
         return set_error(ZM_ERR_INVALID, "double-word derivative: rows per CTA do not divide the side");
     const size_t sa = (size_t)phys_host(G.n2 << ra) * sizeof(ulonglong2);
@@ -634,13 +653,8 @@ int df_derivative(zm_ctx *c, const double *y)
                         : FftLaunch<A>::a(G.n1, ra, sa, c->stream, w, U2(c->tw2), U2(c->fa));
     });
     if (c->twh) {  // Hermitian inverse: half the columns back along alpha1, then real rows
-#ifndef ZM_DF_CH_ROWS_SHIFT
-#define ZM_DF_CH_ROWS_SHIFT 1
-#endif
-        // pass C_h rows per CTA: half the usual budget (2048 values), so that the half-length rows
-        // make twice as many, smaller CTAs (1024 rather than 512 at 2048^2: 1.3 waves were left)
-        const int rbh = std::max(1, lrows_for(s1.A, G.n2));  // a column pair: rows >= 2
-        const int rch = std::max(0, lrows_for(s2.A - 1, G.n1) - ZM_DF_CH_ROWS_SHIFT);
+        const int rbh = std::max(1, lrows_grid(s1.A, G.n2));  // a column pair: rows >= 2
+        const int rch = lrows_grid(s2.A - 1, G.n1, ZM_DF_MINGRID_CH);
         const size_t sbh = (size_t)phys_host(G.n1 << rbh) * sizeof(ulonglong2);
         const size_t sch = (size_t)phys_host((G.n2 / 2) << rch) * sizeof(ulonglong2);
         if (!rc) rc = with_log2(s1.A, [&](auto lc) {

@@ -401,6 +401,18 @@ int rows_for(int L)
     return r;
 }
 
+// Rows per CTA, halved (down to one) while the pass would launch fewer than ZM_FFT_MINGRID CTAs
+// over its `avail` rows, so that small meshes spread over every SM.
+#ifndef ZM_FFT_MINGRID
+#define ZM_FFT_MINGRID 304  // two CTAs per SM of the 152
+#endif
+int rows_grid(int L, int avail)
+{
+    int r = rows_for(L);
+    while (r > 1 && avail / r < ZM_FFT_MINGRID) r >>= 1;
+    return r;
+}
+
 // Largest row held in shared memory by one CTA: 8192 complex doubles (128 KiB).
 constexpr int kMaxSide = 8192;
 
@@ -436,7 +448,7 @@ int launch_passes(zm_ctx *c, const double *w)
 {
     const Geom &g = c->geom;
     const Side s1 = make_side(g.n1, c->tw1, c->twl1), s2 = make_side(g.n2, c->tw2, c->twl2);
-    const int ra = rows_for(g.n2), rb = rows_for(g.n1);
+    const int ra = rows_grid(g.n2, g.n1), rb = rows_grid(g.n1, g.n2);
     if (g.n1 % ra || g.n2 % rb) return set_error(ZM_ERR_INVALID, "Riesz pass: rows per CTA do not divide the side");
     pass_a<kMix><<<g.n1 / ra, kFftTpb, ra * g.n2 * sizeof(double2), c->stream>>>(g.n1, g.n2, s2, ra, w, c->fa);
     pass_b<kMix><<<g.n2 / rb, kFftTpb, rb * g.n1 * sizeof(double2), c->stream>>>(

@@ -129,6 +129,13 @@ int zm_autotune(zm_ctx *ctx, const char *cache_path, int32_t *chosen);
  * FP32C bound.  Other contexts: *tp1 = *tp2 = *chunk = 0. */
 int zm_autotune_tiles(zm_ctx *ctx, const char *cache_path, int32_t *tp1, int32_t *tp2, int32_t *chunk);
 
+/* Set (get) the tile shape of an FP32C high- or medium-order context: the mesh patch of 256
+ * nodes a target or source tile covers, (tp1, tp2) one of (16,16), (8,32), (32,8), (4,64),
+ * (64,4) (see zm_batch_set_tile_shape).  Results change within the FP32C bound.  Returns
+ * ZM_ERR_INVALID for another shape, ZM_ERR_UNSUPPORTED for other contexts. */
+int zm_set_tile_shape(zm_ctx *ctx, int32_t tp1, int32_t tp2);
+int zm_get_tile_shape(zm_ctx *ctx, int32_t *tp1, int32_t *tp2);
+
 /* Wait for the context's stream; reports ZM_ERR_TIMEOUT / ZM_ERR_CUDA raised by its kernels. */
 int zm_sync(zm_ctx *ctx);
 

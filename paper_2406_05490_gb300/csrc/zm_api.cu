@@ -95,6 +95,8 @@ int batch_keep_phi(Batch *b, int on);
 int batch_set_cutoff(Batch *b, int index, double cutoff);
 int batch_autotune(Batch *b, const char *path, int *chosen, float *ms);
 int batch_autotune_tiles(Batch *b, const char *path, int *tp1, int *tp2, int *chunk, float *ms);
+int batch_set_tile_shape(Batch *b, int tp1, int tp2);
+int batch_get_tile_shape(Batch *b, int *tp1, int *tp2);
 
 static int stage_index(zm_ctx *c, const double *y) { return y == c->y0 ? 0 : (y == c->ya ? 1 : 2); }
 
@@ -569,6 +571,25 @@ int zm_autotune_tiles(zm_ctx *c, const char *cache_path, int32_t *tp1, int32_t *
     if (tp1) *tp1 = a;
     if (tp2) *tp2 = b;
     if (chunk) *chunk = k;
+    return rc;
+}
+
+int zm_set_tile_shape(zm_ctx *c, int32_t tp1, int32_t tp2)
+{
+    if (!c) return set_error(ZM_ERR_INVALID, "zm_set_tile_shape: null context");
+    if (!c->batch) return set_error(ZM_ERR_UNSUPPORTED, "zm_set_tile_shape: tiles belong to FP32C high/medium contexts");
+    batch_bind(c->batch, c->stream, &c->prof);
+    return batch_set_tile_shape(c->batch, tp1, tp2);
+}
+
+int zm_get_tile_shape(zm_ctx *c, int32_t *tp1, int32_t *tp2)
+{
+    if (!c || !tp1 || !tp2) return set_error(ZM_ERR_INVALID, "zm_get_tile_shape: null argument");
+    if (!c->batch) return set_error(ZM_ERR_UNSUPPORTED, "zm_get_tile_shape: tiles belong to FP32C high/medium contexts");
+    int a = 0, b = 0;
+    const int rc = batch_get_tile_shape(c->batch, &a, &b);
+    *tp1 = a;
+    *tp2 = b;
     return rc;
 }
 

@@ -667,6 +667,20 @@ int batch_keep_phi(Batch *b, int on)
     return b->plan();
 }
 int batch_autotune(Batch *b, const char *path, int *chosen, float *ms) { return b->autotune(path, chosen, ms); }
+int batch_get_tile_shape(Batch *b, int *tp1, int *tp2)
+{
+    *tp1 = kShapes[b->shape][0];
+    *tp2 = kShapes[b->shape][1];
+    return ZM_OK;
+}
+
+int batch_set_tile_shape(Batch *b, int tp1, int tp2)
+{
+    for (int k = 0; k < kNumShapes; ++k)
+        if (kShapes[k][0] == tp1 && kShapes[k][1] == tp2) return b->set_shape(k);
+    return set_error(ZM_ERR_INVALID, "tile shape (tp1, tp2) must be (16,16), (8,32), (32,8), (4,64) or (64,4)");
+}
+
 int batch_autotune_tiles(Batch *b, const char *path, int *tp1, int *tp2, int *chunk, float *ms)
 {
     int k = 0;
@@ -826,10 +840,7 @@ int zm_batch_autotune(zm_batch *bt, const char *cache_path, int32_t *chosen, flo
 int zm_batch_set_tile_shape(zm_batch *bt, int32_t tp1, int32_t tp2)
 {
     if (!bt) return set_error(ZM_ERR_INVALID, "zm_batch_set_tile_shape: null batch");
-    for (int k = 0; k < kNumShapes; ++k)
-        if (kShapes[k][0] == tp1 && kShapes[k][1] == tp2) return bt->b.set_shape(k);
-    return set_error(ZM_ERR_INVALID,
-                     "zm_batch_set_tile_shape: (tp1, tp2) must be (16,16), (8,32), (32,8), (4,64) or (64,4)");
+    return batch_set_tile_shape(&bt->b, tp1, tp2);
 }
 
 int zm_batch_get_tile_shape(zm_batch *bt, int32_t *tp1, int32_t *tp2)

@@ -100,6 +100,8 @@ def load():
             "zm_wait_selftest": (I, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(D)]),
             "zm_wait_poll_limit": (ctypes.c_int64, []),
             "zm_checked_build": (I, []),
+            "zm_set_tile_shape": (I, [VP, ctypes.c_int32, ctypes.c_int32]),
+            "zm_get_tile_shape": (I, [VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
             "zm_bounds_status": (I, [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
             "zm_br_velocity_noalloc": (I, [ctypes.c_int32, VP, VP, D, VP, VP, VP]),
@@ -358,6 +360,16 @@ def zm_autotune_tiles(h, cache_path=None):
     p = cache_path.encode() if cache_path else None
     _check(load().zm_autotune_tiles(h, p, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return (a.value, b.value), c.value
+
+
+def zm_set_tile_shape(h, tp1, tp2):
+    _check(load().zm_set_tile_shape(h, int(tp1), int(tp2)))
+
+
+def zm_get_tile_shape(h):
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().zm_get_tile_shape(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def zm_batch_set_tile_shape(h, tp1, tp2):

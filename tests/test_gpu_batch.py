@@ -251,3 +251,29 @@ def test_bench_batch_of_64_sampled(zm):
         print(f"batch of 64, interface {k} ({r.n}^2): rel L2 z={ez:.3e} w={ew:.3e} (z - z0)={dz:.3e}")
         assert ez <= TOL32 and ew <= TOL32 and dz <= 1e-5
     zm.zm_batch_destroy(h)
+
+
+def test_context_tile_shape(zm):
+    """zm_set_tile_shape / zm_get_tile_shape on a single FP32C context (a batch of one): every
+    shape stays within the FP32C bound of the oracle; other shapes and FP64 contexts are refused."""
+    n1, n2 = 32, 128
+    z, w = inputs.random_state(n1, n2, seed=29)
+    delta = 0.1 / n2
+    u_ref, wd_ref = oracle.derivative(oracle.Mesh(n1, n2, periodic=True), z, w, 0.5, 1.3, 0.0, delta)
+    m = zm.ZModel(n1, n2, periodic=True, atwood=0.5, g=1.3, delta=delta, fp32c=True)
+    assert zm.zm_get_tile_shape(m.h) == (16, 16)
+    for shape in SHAPES:
+        zm.zm_set_tile_shape(m.h, *shape)
+        assert zm.zm_get_tile_shape(m.h) == shape
+        u, wd = m.velocity(z, w)
+        print(f"context tiles {shape}: rel L2 u={rel(u, u_ref):.3e} wdot={rel(wd, wd_ref):.3e}")
+        assert rel(u, u_ref) <= TOL32 and rel(wd, wd_ref) <= TOL32
+    with pytest.raises(zm.ZMError) as e:
+        zm.zm_set_tile_shape(m.h, 16, 8)
+    assert e.value.code == zm.ZM_ERR_INVALID
+    m.close()
+    m64 = zm.ZModel(n1, n2, periodic=True, atwood=0.5, g=1.3, delta=delta)
+    with pytest.raises(zm.ZMError) as e:
+        zm.zm_set_tile_shape(m64.h, 8, 32)
+    assert e.value.code == zm.ZM_ERR_UNSUPPORTED
+    m64.close()

@@ -48,6 +48,13 @@ MUTANTS = [
     ("medium order takes the wrong velocity for Phi", "zmo_phi(N, z, w, h, u_low ? u_low : u, prm->g, phi);",
      "zmo_phi(N, z, w, h, u, prm->g, phi);"),
     ("RK3 stage uses old state", "b[stage] * (y[k] + dt * ydot[k])", "b[stage] * (y0[k] + dt * ydot[k])"),
+    # the general-length FFT (sides that are not powers of two)
+    ("prime-length DFT root index", "(size_t)((long long)t * k % n) * scale", "(size_t)((long long)t * (k + 1) % n) * scale"),
+    ("Cooley-Tukey twiddle index", "(size_t)((long long)q * k % n) * scale", "(size_t)((long long)q * k % m) * scale"),
+    ("Cooley-Tukey sub-transform index", "sub[(size_t)q * m + k % m], ai", "sub[(size_t)q * m + k / p], ai"),
+    ("general-length roots without the sign", "const double ang = sign * 2.0 * ZMO_PI * t / n;",
+     "const double ang = -2.0 * ZMO_PI * t / n;"),
+    ("signed frequency of odd sides", "return 2 * idx < n ? idx : idx - n;", "return idx < n / 2 ? idx : idx - n;"),
 ]
 
 

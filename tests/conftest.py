@@ -25,3 +25,19 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session", autouse=True)
+def checked_build_reports_no_violation():
+    """With ZM_LIB=checked the whole suite runs on the checked build (libzm_checked.so, whose
+    kernels count out-of-range indices instead of accessing them); at the end of the session
+    the count must be zero."""
+    yield
+    if os.environ.get("ZM_LIB") != "checked":
+        return
+    from paper_2406_05490_gb300 import zm
+    if zm._lib is None:  # no test loaded the library
+        return
+    hits, first, line = zm.zm_bounds_status(clear=True)
+    assert zm.zm_checked_build() and hits == 0, \
+        f"checked build: {hits} index violations, first index {first} at source line {line}"

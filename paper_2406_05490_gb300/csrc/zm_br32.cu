@@ -46,7 +46,10 @@ namespace {
 constexpr int kTs = 256;        // sources per tile (and targets per target tile)
 constexpr int kR = ZM_BR32_R;   // targets per thread
 constexpr int kT = kTs / kR;    // threads per CTA: one target tile per CTA
-constexpr float kFarFactor = 1.25f;
+#ifndef ZM_BR32_FAR
+#define ZM_BR32_FAR 1.25f  // far path when the sphere centres are this many times the radii apart
+#endif
+constexpr float kFarFactor = ZM_BR32_FAR;
 
 // compile-time tuning: unroll of the far loop over source pairs, and the minimum resident CTAs
 // per SM the register allocation must allow

@@ -606,6 +606,16 @@ def run_gb300(args):
     if not args.no_extras:
         # plain FP64 comparator: the same interface, FP64 pair terms
         m64 = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, fp32c=False)
+        # the headline's FP32C derivative against the FP64 path on the same interface with
+        # vorticity (w = 0 makes the velocity vanish), per field: the accuracy side of the
+        # FP32C-vs-FP64 comparison (the oracle parity itself is in the tests)
+        zq, wq = z0, inputs.random_state(n, seed=1)[1]
+        m32 = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, fp32c=True)
+        u32, wd32 = m32.velocity(zq, wq)
+        m32.close()
+        u64, wd64 = m64.velocity(zq, wq)
+        rl2 = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        extras["fp32c_vs_fp64_rel_l2"] = {"u": rl2(u32, u64), "wdot": rl2(wd32, wd64)}
         m64.set_state(z0, w0)
         k64 = 2
         ms64, prof64 = timed_steps(m64, zm, torch, k64, 1, flush)

@@ -665,8 +665,14 @@ def run_gb300(args):
         ms_.set_state(zs, wsn)
         k1 = 10
         ms1, _ = timed_steps(ms_, zm, torch, k1, 3, flush, profile=False)
+        # per-stage kernel times from a second, event-profiled run (plain launches: profiling
+        # replaces the graph replay, so these add up to more than the replayed step)
+        ms1p, prof1 = timed_steps(ms_, zm, torch, k1, 1, flush, profile=True)
         ms_.close()
-        extras["single_mode_32_fp64"] = {"steps_per_s": k1 / (ms1 * 1e-3), "ms_per_step": ms1 / k1}
+        extras["single_mode_32_fp64"] = {"steps_per_s": k1 / (ms1 * 1e-3), "ms_per_step": ms1 / k1,
+                                         "profiled_ms_per_step": ms1p / k1,
+                                         "kernel_us_per_stage": {k: 1e3 * v / (3 * k1) for k, v in prof1["ms"].items()
+                                                                 if prof1["launches"][k]}}
         # medium order (BR velocity moves the interface, FFT velocity drives the vorticity),
         # 256^2 periodic, FP32C pair terms
         mm = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, order=zm.ZM_ORDER_MEDIUM,

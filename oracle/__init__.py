@@ -84,6 +84,7 @@ def _load():
                 "zmo_sheet_strength": (None, [sz, _P, _P, _P, _P]),
                 "zmo_br_velocity": (None, [sz, _P, sz, _P, _P, d, d, _P]),
                 "zmo_br_velocity_cutoff": (None, [sz, _P, sz, _P, _P, d, d, d, _P]),
+                "zmo_within_cutoff": (i, [_P, sz, _P, sz, d]),
                 "zmo_fft2": (None, [i, i, _P, _P, i]),
                 "zmo_riesz_scalar": (None, [M, _P, _P]),
                 "zmo_phi": (None, [sz, _P, _P, _P, _P, d, _P]),
@@ -185,8 +186,7 @@ def br_velocity(zt, zs, gamma, weight, delta):
 
 
 def br_velocity_cutoff(zt, zs, gamma, weight, delta, cutoff):
-    """br_velocity over the sources within `cutoff` of each target (decision in FP32, see
-    zm_oracle.c)."""
+    """br_velocity over the sources with |zt_i - zs_j| <= cutoff (decided in FP64)."""
     lib = _load()
     zt = _arr(zt)
     zs = _arr(zs)
@@ -196,6 +196,13 @@ def br_velocity_cutoff(zt, zs, gamma, weight, delta, cutoff):
     lib.zmo_br_velocity_cutoff(nt, _ptr(zt), ns, _ptr(zs), _ptr(gamma), float(weight), float(delta),
                                float(cutoff), _ptr(u))
     return u
+
+
+def within_cutoff(zi, zj, cutoff):
+    """The oracle's in/out decision for one pair: |zi - zj|^2 <= cutoff^2 in FP64."""
+    lib = _load()
+    a, b = _arr(zi, (3,)), _arr(zj, (3,))
+    return bool(lib.zmo_within_cutoff(_ptr(a), 1, _ptr(b), 1, float(cutoff)))
 
 
 def fft2(re, im, sign):

@@ -29,10 +29,8 @@
  *     Sides of any length: radix-2 for powers of two, otherwise Cooley-Tukey on the smallest
  *     prime factor with prime lengths summed by the definition of the DFT.
  *   Cutoff (Sec. 3.2.2 CutoffBRSolver: only the points within a 3D distance of each point):
- *     the same sum restricted to |z_i - z_j| <= cutoff.  Whether a pair is in is a yes/no
- *     decision taken in the precision of the GPU kernel: with zh = fl32(z), zl = fl32(z - zh),
- *     r = (zh_j - zh_i) + (zl_j - zl_i) per component in FP32 and |r|^2 = fma(rx, rx,
- *     fma(ry, ry, rz * rz)) in FP32, the pair is in iff |r|^2 <= fl32(cutoff^2).
+ *     the same sum restricted to the sources with |z_i - z_j| <= cutoff, decided in FP64 on the
+ *     squared distance of the componentwise differences, |z_i - z_j|^2 <= cutoff^2.
  *   Medium order (Sec. 2: couples the FFT and far-field solvers; Sec. 6: uses FFTs for the
  *     change in vorticity): dz/dt = u from the Birkhoff-Rott sum, while Phi (hence dw/dt) takes
  *     the low-order velocity.
@@ -215,17 +213,16 @@ void zmo_br_velocity(size_t nt, const double *zt, size_t ns, const double *zs,
     }
 }
 
-/* Cutoff decision for target z_i and source z_j (component stride si, sj), FP32 as stated. */
+/* Cutoff decision (Sec. 3.2.2): source z_j (component stride sj) counts for target z_i
+ * (stride si) iff its distance is at most the cutoff, |z_i - z_j|^2 <= cutoff^2 in FP64. */
 int zmo_within_cutoff(const double *zi, size_t si, const double *zj, size_t sj, double cutoff)
 {
-    float r[3];
+    double dist2 = 0.0;
     for (int c = 0; c < 3; c++) {
-        float hi = (float)zi[c * si], hj = (float)zj[c * sj];
-        float li = (float)(zi[c * si] - (double)hi), lj = (float)(zj[c * sj] - (double)hj);
-        r[c] = (hj - hi) + (lj - li);
+        double d = zi[c * si] - zj[c * sj];
+        dist2 += d * d;
     }
-    float r2 = fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]));
-    return r2 <= (float)(cutoff * cutoff);
+    return dist2 <= cutoff * cutoff;
 }
 
 void zmo_br_velocity_cutoff(size_t nt, const double *zt, size_t ns, const double *zs,

@@ -44,7 +44,13 @@ MUTANTS = [
     ("viscosity sign", "+= mu * tmp[p]", "-= mu * tmp[p]"),
     ("low-order velocity sign", "-0.5 * s[p] * nrm", "0.5 * s[p] * nrm"),
     ("RK3 weight", "{1.0, 0.25, 2.0 / 3.0}", "{1.0, 0.5, 2.0 / 3.0}"),
-    ("cutoff test reversed", "return r2 <= (float)(cutoff * cutoff);", "return r2 >= (float)(cutoff * cutoff);"),
+    ("cutoff test reversed", "return dist2 <= cutoff * cutoff;", "return dist2 >= cutoff * cutoff;"),
+    ("cutoff boundary exclusive", "return dist2 <= cutoff * cutoff;", "return dist2 < cutoff * cutoff;"),
+    ("cutoff decided in FP32", "return dist2 <= cutoff * cutoff;",
+     "return (float)dist2 <= (float)(cutoff * cutoff);"),
+    ("cutoff against the unsquared distance", "return dist2 <= cutoff * cutoff;", "return dist2 <= cutoff;"),
+    ("cutoff distance drops a component", "for (int c = 0; c < 3; c++) {\n        double d = zi",
+     "for (int c = 0; c < 2; c++) {\n        double d = zi"),
     ("medium order takes the wrong velocity for Phi", "zmo_phi(N, z, w, h, u_low ? u_low : u, prm->g, phi);",
      "zmo_phi(N, z, w, h, u, prm->g, phi);"),
     ("RK3 stage uses old state", "b[stage] * (y[k] + dt * ydot[k])", "b[stage] * (y0[k] + dt * ydot[k])"),

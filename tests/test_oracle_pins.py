@@ -332,6 +332,30 @@ def test_cutoff_sum_decomposes_the_exact_sum():
     assert np.all(oracle.br_velocity_cutoff(z, z, gam, wt, de, 1e-6) == 0.0)
 
 
+def test_cutoff_boundary_is_the_fp64_distance():
+    """Sec. 3.2.2 counts the sources within the cutoff distance: a source at exactly the cutoff
+    is in, and sources 2^-40 (relative) inside and outside the cutoff are in and out.  FP32
+    cannot tell the three distances apart (they round to the same float), so an FP32 decision,
+    a strict inequality or an unsquared comparison each fail here."""
+    c = 0.25
+    zt = np.zeros((3, 1))
+    eps = 2.0 ** -40
+    for x, want_in in ((c, True), (c * (1 - eps), True), (c * (1 + eps), False),
+                       (c * 0.5, True), (c * 1.5, False)):
+        zs = np.array([[x], [0.0], [0.0]])
+        gam = np.array([[0.0], [0.0], [1.0]])
+        u = oracle.br_velocity_cutoff(zt, zs, gam, 1.0, 0.01, c)
+        ref = oracle.br_velocity(zt, zs, gam, 1.0, 0.01)
+        assert ref[1, 0] != 0.0
+        assert np.array_equal(u, ref if want_in else np.zeros_like(ref)), (x, want_in)
+        assert oracle.within_cutoff(zt[:, 0], zs[:, 0], c) == want_in
+    # the decision uses all three components: (0.15, 0.2, 0) lies at 0.25 up to rounding, and
+    # (0.15, 0.2, 0.01) clearly outside
+    assert not oracle.within_cutoff([0, 0, 0], [0.15, 0.2, 0.01], c)
+    assert oracle.within_cutoff([0, 0, 0], [0.15, 0.2, 0.0], c * (1 + 1e-12))
+    assert oracle.within_cutoff([1.0, 2.0, 3.0], [1.0, 2.0, 3.0 + c * (1 - 1e-9)], c)
+
+
 # ------------------------------------------------------------------------------------------
 # Riesz transform / FFT
 # ------------------------------------------------------------------------------------------

@@ -41,18 +41,21 @@ ORDER_MEDIUM = 1
 ORDER_HIGH = 2
 
 
-def build(force: bool = False) -> str:
-    """Compile zm_oracle.c into oracle/_build/liboracle.so (gcc, no FMA contraction)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile zm_oracle.c into oracle/_build/liboracle.so (gcc, no FMA contraction); with
+    openmp=True the same source into liboracle_omp.so, whose Birkhoff-Rott sums split their
+    targets across threads (same bits; used to write stored expected states)."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    stale = (not os.path.exists(_LIB)
-             or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+    lib = os.path.join(_LIBDIR, "liboracle_omp.so") if openmp else _LIB
+    stale = (not os.path.exists(lib)
+             or os.path.getmtime(lib) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
     if force or stale:
-        tmp = _LIB + f".tmp{os.getpid()}"
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
-               "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+               "-fno-fast-math"] + (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 class _Mesh(ctypes.Structure):

@@ -41,7 +41,9 @@
  *       y1 = y + dt L(y);  y2 = 3/4 y + 1/4 (y1 + dt L(y1));  y' = 1/3 y + 2/3 (y2 + dt L(y2)).
  *
  * All arithmetic is IEEE FP64, compiled without FMA contraction; sums over sources use
- * Neumaier-compensated accumulation.
+ * Neumaier-compensated accumulation.  The default build is serial; an OpenMP build of this same
+ * file (liboracle_omp.so) splits only the targets of the Birkhoff-Rott sums across threads and
+ * returns the same bits.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -196,6 +198,9 @@ void zmo_br_velocity(size_t nt, const double *zt, size_t ns, const double *zs,
 {
     double pref = -weight / (4.0 * ZMO_PI);
     double d2 = delta * delta;
+    /* Targets are independent and each one's sum runs in the same order either way, so an
+     * OpenMP build (used only to write stored expected states faster) gives identical bits. */
+#pragma omp parallel for schedule(dynamic, 64)
     for (size_t i = 0; i < nt; i++) {
         nsum acc[3] = {{0, 0}, {0, 0}, {0, 0}};
         double xi = zt[i], yi = zt[nt + i], wi = zt[2 * nt + i];
@@ -231,6 +236,7 @@ void zmo_br_velocity_cutoff(size_t nt, const double *zt, size_t ns, const double
 {
     double pref = -weight / (4.0 * ZMO_PI);
     double d2 = delta * delta;
+#pragma omp parallel for schedule(dynamic, 64)
     for (size_t i = 0; i < nt; i++) {
         nsum acc[3] = {{0, 0}, {0, 0}, {0, 0}};
         double xi = zt[i], yi = zt[nt + i], wi = zt[2 * nt + i];

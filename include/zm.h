@@ -265,12 +265,14 @@ void zm_batch_destroy(zm_batch *b);
 
 /* ---- serving: continuous batching of solve requests ------------------------------------- */
 
-/* A worker thread owned by the server admits submitted requests in arrival order as slots
- * (max_slots) and device memory (mem_budget_bytes, counted per request from its mesh size)
- * free up, keeps every admitted interface's state resident, advances all resident interfaces
- * together by one RK3 step per iteration (the batched FP32C path) and retires finished ones
- * between iterations, so requests arriving while others run join the next iteration.  A
- * request's result does not depend on the others (bitwise).  The paper has no serving form. */
+/* A worker thread owned by the server admits submitted requests as slots (max_slots) and
+ * device memory (mem_budget_bytes, counted per request from its mesh size) free up, keeps every
+ * admitted interface's state resident, advances resident interfaces by one RK3 step per
+ * iteration (the batched FP32C path, all of them in one set of launches) and retires finished
+ * ones between iterations, so requests arriving while others run join the next iteration.  A
+ * request's result does not depend on the others (bitwise).  Which requests are admitted and
+ * advanced follows the scheduling policy (zm_server_set_policy; default ZM_SERVE_ALL).  The
+ * paper has no serving form. */
 #define ZM_REQ_QUEUED 0
 #define ZM_REQ_RUNNING 1
 #define ZM_REQ_DONE 2
@@ -310,6 +312,22 @@ int zm_server_result(zm_server *s, int64_t id, double *z, double *w, double *lat
 /* Cancel a request: a queued one fails at once, a running one leaves at the next iteration. */
 int zm_server_cancel(zm_server *s, int64_t id);
 int zm_server_get_stats(zm_server *s, zm_server_stats *out);
+
+/* Scheduling policy, changeable at any time (applies from the next iteration):
+ * ZM_SERVE_ALL   admission first come, first served (the head of the queue waits until it
+ *                fits); every resident interface advances one step per iteration.
+ *                pairs_per_iteration is ignored.
+ * ZM_SERVE_SRPT  shortest remaining work first: queued requests are admitted least total work
+ *                (pair interactions) first wherever they fit; each iteration advances the
+ *                resident interfaces with the least remaining work first, adding them while the
+ *                iteration's pair interactions stay within pairs_per_iteration (<= 0: no cap;
+ *                always at least one interface).  Small requests overtake large ones, which
+ *                bounds their latency under overload; under endless overload the largest
+ *                requests can starve.
+ * Results do not depend on the policy (bitwise).  ZM_ERR_INVALID for an unknown policy. */
+#define ZM_SERVE_ALL 0
+#define ZM_SERVE_SRPT 1
+int zm_server_set_policy(zm_server *s, int32_t policy, int64_t pairs_per_iteration);
 /* Stop the worker and free everything (requests still queued or running are dropped). */
 void zm_server_destroy(zm_server *s);
 

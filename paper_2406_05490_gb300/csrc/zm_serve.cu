@@ -6,6 +6,18 @@
 // to the host, memory returned) between iterations, so requests that arrive while others run
 // join the next iteration.  Per-interface results do not depend on the mix (exact fixed-point
 // accumulation).  The paper has no serving form: it runs one interface per job (Sec. 4-5).
+//
+// Scheduling policies (zm_server_set_policy):
+//   ZM_SERVE_ALL   admission first come, first served; every resident interface advances one
+//                  step per iteration.  Under overload every request then finishes near the
+//                  makespan: each iteration costs as much as stepping the whole resident set.
+//   ZM_SERVE_SRPT  shortest remaining work first: queued requests are admitted least total
+//                  work first wherever they fit, and each iteration advances the resident
+//                  interfaces with the least remaining work (pairs left) first, as many as fit
+//                  a cap of pair interactions per iteration (always at least one).  Small
+//                  requests overtake large ones at iteration granularity; with a finite trace
+//                  every request finishes, but under endless overload the largest can starve.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -41,6 +53,8 @@ struct Request {
     int status = ZM_OK;
     bool cancel = false;
     double t_submit = 0, t_admit = 0, t_done = 0;
+    // Birkhoff-Rott pair interactions still to evaluate (three evaluations per step)
+    int64_t work() const { return 3LL * remaining * ((int64_t)mesh.n1 * mesh.n2) * ((int64_t)mesh.n1 * mesh.n2); }
 };
 
 }  // namespace
@@ -49,6 +63,8 @@ class Server {
 public:
     size_t budget = 0, used = 0, peak_used = 0;
     int max_slots = 0, peak_slots = 0;
+    int policy = ZM_SERVE_ALL;
+    int64_t pairs_cap = 0;  // SRPT: pair interactions per iteration (<= 0: no cap)
     double g = 1.0, mu = 0.0;
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -107,8 +123,9 @@ public:
     void loop()
     {
         cudaSetDevice(device);
-        std::vector<Request *> admitted, finished;
-        int stable = 0;  // iterations since the resident set last changed
+        std::vector<Request *> admitted, finished, sel;
+        std::vector<int64_t> sel_ids, prev_ids;  // the stepped set of this and the last iteration
+        int stable = 0;  // iterations since the stepped set last changed
         while (true) {
             admitted.clear();
             {
@@ -128,18 +145,33 @@ public:
                         ++it;
                     }
                 }
-                // first come, first served: the head waits until it fits
-                while (!queue.empty() && (int)(running.size() + admitted.size()) < max_slots &&
-                       used + queue.front()->bytes <= budget) {
-                    Request *r = queue.front();
-                    queue.pop_front();
-                    used += r->bytes;
-                    admitted.push_back(r);
+                if (policy == ZM_SERVE_SRPT) {
+                    // least total work first (arrival order among equals), wherever it fits
+                    std::stable_sort(queue.begin(), queue.end(),
+                                     [](const Request *a, const Request *b) { return a->work() < b->work(); });
+                    for (auto it = queue.begin();
+                         it != queue.end() && (int)(running.size() + admitted.size()) < max_slots;) {
+                        if (used + (*it)->bytes <= budget) {
+                            used += (*it)->bytes;
+                            admitted.push_back(*it);
+                            it = queue.erase(it);
+                        } else {
+                            ++it;
+                        }
+                    }
+                } else {
+                    // first come, first served: the head waits until it fits
+                    while (!queue.empty() && (int)(running.size() + admitted.size()) < max_slots &&
+                           used + queue.front()->bytes <= budget) {
+                        Request *r = queue.front();
+                        queue.pop_front();
+                        used += r->bytes;
+                        admitted.push_back(r);
+                    }
                 }
                 peak_used = std::max(peak_used, used);
             }
             const double t0 = now_s();
-            bool changed = !admitted.empty();
             for (Request *r : admitted) {
                 int rc = Batch::alloc_inst(r->inst, r->mesh, r->atwood, g, mu, r->delta, r->dt, stream,
                                            true, &r->slab);
@@ -168,22 +200,42 @@ public:
                     r->remaining = 0;
                     r->status = ZM_ERR_INVALID;
                 }
-            if (changed || batch.h.size() != running.size()) {
+            // the interfaces this iteration advances
+            sel.clear();
+            for (Request *r : running)
+                if (r->remaining > 0) sel.push_back(r);
+            if (policy == ZM_SERVE_SRPT) {
+                std::stable_sort(sel.begin(), sel.end(),
+                                 [](const Request *a, const Request *b) { return a->work() < b->work(); });
+                if (pairs_cap > 0) {
+                    int64_t acc = 0;
+                    size_t k = 0;
+                    for (; k < sel.size(); ++k) {
+                        const int64_t nn = (int64_t)sel[k]->mesh.n1 * sel[k]->mesh.n2;
+                        const int64_t step_pairs = 3 * nn * nn;
+                        if (k > 0 && acc + step_pairs > pairs_cap) break;
+                        acc += step_pairs;
+                    }
+                    sel.resize(k);
+                }
+            }
+            sel_ids.clear();
+            for (Request *r : sel) sel_ids.push_back(r->id);
+            if (sel_ids != prev_ids) {
                 batch.h.clear();
-                for (Request *r : running) batch.h.push_back(r->inst);
+                for (Request *r : sel) batch.h.push_back(r->inst);
                 int rc = batch.plan();  // drops the captured step graph
                 if (rc) {
                     fail_all(rc);
                     continue;
                 }
+                prev_ids.swap(sel_ids);
                 stable = 0;
             } else {
                 ++stable;
             }
             peak_slots = std::max(peak_slots, (int)running.size());
-            bool any_work = false;
-            for (Request *r : running) any_work |= r->remaining > 0;
-            if (any_work) {
+            if (!sel.empty()) {
                 // plain launches right after a membership change; once the same set has run an
                 // iteration, the step is captured as a graph and replayed until the set changes
                 int rc;
@@ -196,8 +248,8 @@ public:
                     continue;
                 }
                 ++steps;
-                for (Request *r : running) {
-                    if (r->remaining > 0) r->remaining -= 1;
+                for (Request *r : sel) {
+                    r->remaining -= 1;
                     pairs += 3LL * r->inst.geom.N * r->inst.geom.N;
                 }
             }
@@ -258,6 +310,14 @@ public:
         running.clear();
         batch.h.clear();
         cv_done.notify_all();
+    }
+
+    int set_policy(int p, int64_t cap)
+    {
+        std::lock_guard<std::mutex> lk(m);
+        policy = p;
+        pairs_cap = cap;
+        return ZM_OK;
     }
 };
 
@@ -397,6 +457,13 @@ int zm_server_cancel(zm_server *sv, int64_t id)
     }
     sv->s.cv_work.notify_all();
     return ZM_OK;
+}
+
+int zm_server_set_policy(zm_server *sv, int32_t policy, int64_t pairs_per_iteration)
+{
+    if (!sv || (policy != ZM_SERVE_ALL && policy != ZM_SERVE_SRPT))
+        return set_error(ZM_ERR_INVALID, "zm_server_set_policy: bad arguments");
+    return sv->s.set_policy(policy, policy == ZM_SERVE_SRPT ? pairs_per_iteration : 0);
 }
 
 int zm_server_get_stats(zm_server *sv, zm_server_stats *out)

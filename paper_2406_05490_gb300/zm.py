@@ -141,6 +141,7 @@ def load():
             "zm_server_result": (I, [VP, ctypes.c_int64, VP, VP, ctypes.POINTER(D), ctypes.POINTER(D)]),
             "zm_server_cancel": (I, [VP, ctypes.c_int64]),
             "zm_server_get_stats": (I, [VP, ctypes.POINTER(ServerStats)]),
+            "zm_server_set_policy": (I, [VP, ctypes.c_int32, ctypes.c_int64]),
             "zm_server_destroy": (None, [VP]),
         }
         for name, (res, args) in sig.items():
@@ -260,11 +261,31 @@ def zm_wait_poll_limit():
     return int(load().zm_wait_poll_limit())
 
 
+def _numel(x):
+    if isinstance(x, np.ndarray):
+        return x.size
+    if hasattr(x, "numel"):
+        return int(x.numel())
+    return None  # a raw address: the caller vouches for its size
+
+
 def zm_br_velocity_noalloc(n, z, gamma, delta, u, status=None, stream=None):
     """FP64 all-pairs sum on caller-owned device buffers; the library allocates nothing (its
-    workspace is a static device array, shared by all calls; n <= 65536)."""
-    _check(load().zm_br_velocity_noalloc(int(n), ptr(z), ptr(gamma), float(delta), ptr(u),
-                                         None if status is None else status.data_ptr(), stream))
+    workspace is a static device array, shared by all calls; n <= 65536).  z, gamma and u must
+    hold at least 3 n float64 values; status, if given, is an int32 CUDA tensor."""
+    n = int(n)
+    for name, x in (("z", z), ("gamma", gamma), ("u", u)):
+        k = _numel(x)
+        if k is not None and k < 3 * max(n, 0):
+            raise ZMError(ZM_ERR_INVALID, f"zm_br_velocity_noalloc: {name} holds {k} values, needs 3 n = {3 * n}")
+    sp = None
+    if status is not None:
+        import torch
+        if not (isinstance(status, torch.Tensor) and status.dtype == torch.int32 and status.is_cuda
+                and status.numel() >= 1):
+            raise ZMError(ZM_ERR_INVALID, "zm_br_velocity_noalloc: status must be an int32 CUDA tensor")
+        sp = status.data_ptr()
+    _check(load().zm_br_velocity_noalloc(n, ptr(z), ptr(gamma), float(delta), ptr(u), sp, stream))
 
 
 def _profile_dict(p):
@@ -465,6 +486,13 @@ def zm_server_get_stats(h):
     s = ServerStats()
     _check(load().zm_server_get_stats(h, ctypes.byref(s)))
     return {f: getattr(s, f) for f, _ in s._fields_}
+
+
+ZM_SERVE_ALL, ZM_SERVE_SRPT = 0, 1
+
+
+def zm_server_set_policy(h, policy, pairs_per_iteration=0):
+    _check(load().zm_server_set_policy(h, int(policy), int(pairs_per_iteration)))
 
 
 def zm_server_destroy(h):

@@ -99,3 +99,30 @@ def test_failures_stay_local(zm):
     assert e.value.code == zm.ZM_ERR_BUSY
     zm.zm_server_destroy(small)
     zm.zm_server_destroy(srv)
+
+
+def test_srpt_lets_small_requests_overtake_and_keeps_results(zm):
+    """Shortest remaining work first: small requests submitted just after a large one finish
+    before it (the large one advances only when no smaller work fits the per-iteration cap), and
+    every result is still bitwise the solve done alone."""
+    big = (128, *inputs.multi_mode(128, n_modes=4, seed=21), 20)
+    smalls = [(32, *inputs.multi_mode(32, n_modes=4, seed=30 + k), 5) for k in range(4)]
+    srv = zm.zm_server_create(1 << 30, 8, g=1.0)
+    zm.zm_server_set_policy(srv, zm.ZM_SERVE_SRPT, 3 * 128 ** 4 // 2)
+    ids = [zm.zm_server_submit(srv, n, n, z, w, 0.5, 0.1 / n, 1e-3, s) for n, z, w, s in [big] + smalls]
+    for rid in ids:
+        assert zm.zm_server_wait(srv, rid, 120.0) == zm.ZM_OK
+    lat = {}
+    for (n, z0, w0, s), rid in zip([big] + smalls, ids):
+        st, z, w, l, _ = zm.zm_server_result(srv, rid, n * n)
+        assert st == zm.ZM_OK
+        lat[rid] = l
+        za, wa = alone(zm, n, z0, w0, 0.5, 0.1 / n, 1e-3, s)
+        assert np.array_equal(z, za) and np.array_equal(w, wa)
+    zm.zm_server_destroy(srv)
+    assert max(lat[r] for r in ids[1:]) < lat[ids[0]]
+    other = zm.zm_server_create(1 << 20, 1)
+    with pytest.raises(zm.ZMError) as e:
+        zm.zm_server_set_policy(other, 7, 0)
+    assert e.value.code == zm.ZM_ERR_INVALID
+    zm.zm_server_destroy(other)

@@ -167,7 +167,10 @@ static int read_status(zm_ctx *c)
     if (rc) return rc;
     if (h & kErrTimeout) {
         cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
-        return set_error(ZM_ERR_TIMEOUT, "a bounded device-side wait gave up (status word set)");
+        return set_error(ZM_ERR_TIMEOUT, (h & kErrDrain)
+                                             ? "a bounded device-side wait gave up, and so did the wait for "
+                                               "the copies in flight (status word set)"
+                                             : "a bounded device-side wait gave up (status word set)");
     }
     if (c->batch) {
         batch_bind(c->batch, c->stream, &c->prof);

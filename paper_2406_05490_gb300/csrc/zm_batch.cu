@@ -618,7 +618,10 @@ int Batch::status()
     if (!rc) rc = cuda_check(cudaStreamSynchronize(stream), "batch synchronize");
     if (!rc && (hs & kErrTimeout)) {
         cudaMemsetAsync(err, 0, sizeof(int), stream);
-        rc = set_error(ZM_ERR_TIMEOUT, "a bounded device-side wait gave up (status word set)");
+        rc = set_error(ZM_ERR_TIMEOUT, (hs & kErrDrain)
+                                           ? "a bounded device-side wait gave up, and so did the wait for "
+                                             "the copies in flight (status word set)"
+                                           : "a bounded device-side wait gave up (status word set)");
     }
     return rc;
 }

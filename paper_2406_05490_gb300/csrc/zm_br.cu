@@ -13,9 +13,12 @@
 // memory.  Split partial sums go to a [nsplit][3][N] workspace reduced in a fixed order by the
 // reduction kernel, which keeps results deterministic.
 //
-// This file holds the FP64 variant (every operation in FP64, rsqrt from CUDA's double-precision
-// math library) -- the plain per-instance comparator -- and its allocation-free form; the
-// FP32-compensated variant is in zm_br32.cu.
+// This file holds the FP64 variant (every operation in FP64; the kernel (|r|^2 + delta^2)^(-3/2)
+// from the hardware reciprocal-square-root estimate and one second-order correction, see
+// dev::rsqrt_cube) -- the plain per-instance comparator -- and its allocation-free form; the
+// FP32-compensated variant is in zm_br32.cu.  Per pair: 21 FP64 instructions (3 differences,
+// 3 FMAs for |r|^2 + delta^2, 6 for the kernel, 6 for the cross product, 3 accumulations) and
+// one MUFU operation, for 26 counted flops.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -89,8 +92,7 @@ __global__ void __launch_bounds__(kTpb)
                 for (int r = 0; r < kR; ++r) {
                     const double rx = sx - tx[r], ry = sy - ty[r], rz = sz - tz[r];
                     const double q = fma(rx, rx, fma(ry, ry, fma(rz, rz, d2)));
-                    const double iq = rsqrt(q);
-                    const double kk = iq * iq * iq;
+                    const double kk = dev::rsqrt_cube(q);
                     ax[r] = fma(kk, ry * gz - rz * gy, ax[r]);
                     ay[r] = fma(kk, rz * gx - rx * gz, ay[r]);
                     az[r] = fma(kk, rx * gy - ry * gx, az[r]);
@@ -109,11 +111,12 @@ __global__ void __launch_bounds__(kTpb)
     }
     if (bad) {
         if (tid == 0) {
-            atomicOr(err, kErrTimeout);
+            int flags = kErrTimeout;
             // let the copies still in flight (tiles kb and kb + 1) land, again with a bounded
             // wait, before the CTA's shared memory is released
             for (int k = kb; k < kb + 2 && k < nt; ++k)
-                (void)dev::mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1);
+                if (!dev::mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1)) flags |= kErrDrain;
+            atomicOr(err, flags);
         }
         return;
     }
@@ -247,17 +250,20 @@ __global__ void na_pack_kernel(int n, int ntiles, const double *__restrict__ z,
     if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
 }
 
+// A CTA whose bounded wait gave up wrote no partial sums, so the workspace may hold an earlier
+// call's: u is then filled with NaN, which shows the failure even to a caller without `status`.
 __global__ void na_reduce_kernel(int n, int nsplit, const double *__restrict__ part,
                                  double *__restrict__ u, const int *status_in, int32_t *status_out)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool failed = (*status_in & kErrTimeout) != 0;
     if (p < n) {
         double s[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < nsplit; ++k)
             for (int c = 0; c < 3; ++c) s[c] += part[((size_t)k * 3 + c) * n + p];
-        for (int c = 0; c < 3; ++c) u[(size_t)c * n + p] = s[c];
+        for (int c = 0; c < 3; ++c) u[(size_t)c * n + p] = failed ? __longlong_as_double(0x7ff8000000000000LL) : s[c];
     }
-    if (status_out && p == 0) *status_out = (*status_in & kErrTimeout) ? ZM_ERR_TIMEOUT : ZM_OK;
+    if (status_out && p == 0) *status_out = failed ? ZM_ERR_TIMEOUT : ZM_OK;
 }
 
 std::mutex g_na_mutex;
@@ -285,14 +291,17 @@ int na_scratch(double **out)
     return ZM_OK;
 }
 
-bool on_device(const void *p)
+// Device memory of the current device, or managed memory.  Memory of another GPU is refused:
+// without peer access the kernels would fault on it.
+bool on_device(const void *p, int dev)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -310,8 +319,15 @@ extern "C" int zm_br_velocity_noalloc(int32_t n, const double *z, const double *
                          "zm_br_velocity_noalloc: n must be in [1, 65536] (size of the static workspace)");
     if (!z || !gamma || !u || !(delta > 0) || !std::isfinite(delta))
         return set_error(ZM_ERR_INVALID, "zm_br_velocity_noalloc: null pointer or delta <= 0");
-    if (!on_device(z) || !on_device(gamma) || !on_device(u) || (status && !on_device(status)))
-        return set_error(ZM_ERR_INVALID, "zm_br_velocity_noalloc: z, gamma, u, status must be device memory");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ZM_ERR_INVALID, "zm_br_velocity_noalloc: no current CUDA device");
+    }
+    if (!on_device(z, dev) || !on_device(gamma, dev) || !on_device(u, dev) ||
+        (status && !on_device(status, dev)))
+        return set_error(ZM_ERR_INVALID,
+                         "zm_br_velocity_noalloc: z, gamma, u, status must be memory of the current device");
     double *base = nullptr;
     int rc = na_scratch(&base);
     if (rc) return rc;

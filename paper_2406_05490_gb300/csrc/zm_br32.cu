@@ -393,11 +393,13 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
     }
     if (bad) {
         if (tid == 0) {
-            atomicOr(err, kErrTimeout);
+            int flags = kErrTimeout;
             // let copies still in flight (units kb and kb + 1) land before shared memory is
             // released, again with bounded waits
             for (int k = kb; k < kb + 2; ++k)
-                if (unit[k & 1].inst >= 0) (void)dev::mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1);
+                if (unit[k & 1].inst >= 0 && !dev::mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1))
+                    flags |= kErrDrain;
+            atomicOr(err, flags);
         }
         return;
     }

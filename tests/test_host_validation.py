@@ -59,3 +59,15 @@ def test_request_bytes_and_strings(zm):
     for code in range(0, -8, -1):
         assert lib.zm_error_string(code)
     assert zm.zm_checked_build() is False
+
+
+def test_noalloc_rejects_on_the_host(zm):
+    """The allocation-free sum refuses, before any CUDA work: n outside [1, 65536], buffers
+    shorter than 3 n (binding), and, with no GPU, any pointer (none is device memory)."""
+    import numpy as np
+    a = np.zeros((3, 8))
+    assert code_of(zm, lambda: zm.zm_br_velocity_noalloc(65537, a, a, 0.01, a)) == zm.ZM_ERR_INVALID
+    assert code_of(zm, lambda: zm.zm_br_velocity_noalloc(0, a, a, 0.01, a)) == zm.ZM_ERR_INVALID
+    assert code_of(zm, lambda: zm.zm_br_velocity_noalloc(9, a, a, 0.01, a)) == zm.ZM_ERR_INVALID
+    assert code_of(zm, lambda: zm.zm_br_velocity_noalloc(8, a, a, 0.0, a)) == zm.ZM_ERR_INVALID
+    assert code_of(zm, lambda: zm.zm_br_velocity_noalloc(8, a, a, 0.01, a)) == zm.ZM_ERR_INVALID

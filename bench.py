@@ -48,7 +48,7 @@ def _measured_hbm_gbs(default=6795.5):
 
 HBM_GBS = _measured_hbm_gbs()
 FLOPS_PER_PAIR = 26  # direct-formula FP32 flops per pair interaction (FMA = 2; rsqrt on MUFU)
-SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_LANES = 128     # FP32 FMA lanes per SM (for the derived peak beside the measured one)
 CONFIG = {"workload": "multimode-256x256-highorder-fp32c", "n_side": N_SIDE, "points": N_SIDE**2,
           "modes": 16, "order": "high", "precision": "fp32c",
           "pairs_per_step": 3 * N_SIDE**4, "l2": "flushed between timed steps (256 MB write)"}
@@ -62,6 +62,11 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the side runs (FP64, low order, 32^2, batch, serving)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving runs")
+    ap.add_argument("--serve-compare", action="store_true",
+                    help="also serve both traces with the all-resident first-come-first-served policy")
+    ap.add_argument("--case", nargs=3, metavar=("KIND", "SIZE", "STEPS"),
+                    help="run one small fixed workload for a profiler and exit (no timing, no JSON): "
+                         "KIND is low | lowdf | high32 | high64 | batch | single")
     return ap.parse_args()
 
 
@@ -135,6 +140,28 @@ def recorded_traffic(tiles):
     except Exception:
         pass
     return None
+
+
+def fp64_inst_record():
+    """FP64-pipe thread instructions per unit of work per kernel class, counted by ncu on the
+    current kernel sources (profiles/fp64_pipe_instructions.json); an entry whose sources changed
+    since the count is dropped (its fraction is then reported as null)."""
+    p = os.path.join(ROOT, "profiles", "fp64_pipe_instructions.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return {}
+    out = {}
+    for k, e in d.get("entries", {}).items():
+        h = hashlib.sha256()
+        try:
+            for f in e["sources"]:
+                h.update(open(os.path.join(ROOT, f), "rb").read())
+        except Exception:
+            continue
+        if h.hexdigest()[:16] == e.get("source_sha256_16"):
+            out[k] = (float(e["thread_inst"]), e.get("n_side"))
+    return out
 
 
 def dist_setup(args):
@@ -291,6 +318,59 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------------------------
 
+def run_case(kind, size, steps):
+    """A few RK3 steps of one fixed configuration through the C ABI and nothing else, so that a
+    profiler (ncu -k / -s / -c) sees a short, known launch sequence:
+      low SIZE STEPS      low order, FP64, SIZE^2 periodic 8-mode interface with vorticity
+      lowdf SIZE STEPS    the same in double words
+      high32 SIZE STEPS   high order, FP32C pair terms
+      high64 SIZE STEPS   high order, FP64
+      batch COUNT STEPS   COUNT ragged interfaces (sides 64-384), FP32C batch
+      single SIZE STEPS   single mode on free edges, FP64"""
+    import torch
+
+    from paper_2406_05490_gb300 import inputs, zm
+    torch.cuda.set_device(0)
+    if kind == "batch":
+        insts = inputs.ragged_batch(count=size, lo=64, hi=384, n_modes=4, seed=0)
+        h = zm.zm_batch_create([(r.n, r.n, 1.0, 1.0, True) for r in insts], [r.atwood for r in insts],
+                               delta=[0.1 / r.n for r in insts])
+        for k, r in enumerate(insts):
+            zm.zm_batch_set_state(h, k, r.z, inputs.random_state(r.n, seed=k)[1])
+        zm.zm_batch_step(h, 1e-3, steps)
+        zm.zm_batch_sync(h)
+        zm.zm_batch_destroy(h)
+        return 0
+    if kind == "single":
+        z, w = inputs.single_mode(size)
+        model = zm.ZModel(size, periodic=False, atwood=0.5, g=1.0, delta=0.1 / size)
+        model.set_state(z, w)
+        model.step(1e-3, steps)
+        model.sync()
+        model.close()
+        return 0
+    if kind not in ("low", "lowdf", "high32", "high64"):
+        print(run_case.__doc__)
+        return 2
+    order = zm.ZM_ORDER_LOW if kind in ("low", "lowdf") else zm.ZM_ORDER_HIGH
+    z, _ = inputs.multi_mode(size, n_modes=8, seed=7, amp=0.02)
+    _, w = inputs.random_state(size, seed=3)
+    model = zm.ZModel(size, periodic=True, atwood=0.7, g=1.0, order=order, fp32c=(kind == "high32"),
+                      df64=(kind == "lowdf"))
+    model.set_state(z, w)
+    model.step(1e-3, steps)
+    model.sync()
+    model.close()
+    return 0
+
+
+def measured_fp32_peak(zm, reps=3):
+    """The FP32 FMA rate of this GPU measured by the library's probe kernels (scalar FFMA and
+    packed FP32x2 FMA chains on every SM), best of `reps` runs each, in TFLOP/s."""
+    scalar = max(zm.zm_measure_peak(zm.PEAK_FP32) for _ in range(reps)) / 1e12
+    packed = max(zm.zm_measure_peak(zm.PEAK_FP32X2) for _ in range(reps)) / 1e12
+    return max(scalar, packed), {"scalar_ffma": scalar, "packed_ffma2": packed}
+
 def timed_steps(model, zm, torch, steps, warmup, flush, profile=True):
     """Device time of `steps` RK3 steps (CUDA events on the context's stream, L2 flushed
     between steps, flush excluded).  Returns (ms_total, profile dict)."""
@@ -325,10 +405,12 @@ LOW_BYTES = {"geometry": 72, "fft": 144, "vorticity": 152}
 LOW_LAUNCHES_PER_EVAL = {"geometry": 1, "fft": 3, "vorticity": 1}
 
 
-def bench_low_order(zm, torch, inputs, flush, nl, steps, warmup, df64):
+def bench_low_order(zm, torch, inputs, flush, nl, steps, warmup, df64, fp64_tflops=None):
     """Low-order steps on an nl^2 periodic 8-mode interface (amplitude 0.02, A = 0.7): device
     time per step, and per kernel class its time per evaluation and algorithmic HBM GB/s as a
-    fraction of the measured copy bandwidth."""
+    fraction of the measured copy bandwidth; for the FP64 path also the fraction of the FP64
+    pipe it keeps busy (ncu-counted FP64 instructions per point / time / the measured FP64
+    instruction rate), the roofline these kernels actually sit on."""
     zl, wl = inputs.multi_mode(nl, n_modes=8, seed=7, amp=0.02)
     ml = zm.ZModel(nl, periodic=True, atwood=0.7, g=1.0, order=zm.ZM_ORDER_LOW, df64=df64)
     ml.set_state(zl, wl)
@@ -342,6 +424,13 @@ def bench_low_order(zm, torch, inputs, flush, nl, steps, warmup, df64):
         t = profl["ms"][k] / evals
         gbs = b * pts / (t * 1e-3) / 1e9 if t > 0 else 0.0
         kern[k] = {"ms_per_eval": t, "alg_bytes_per_point": b, "alg_gbs": gbs, "hbm_frac": gbs / HBM_GBS}
+        if not df64 and fp64_tflops:
+            inst, side = fp64_inst_record().get(k, (None, None))
+            if side is not None and side != nl:
+                inst = None  # counted on another mesh size (per-point count depends on the side)
+            kern[k]["fp64_inst_per_point"] = inst
+            kern[k]["fp64_pipe_frac"] = (inst * pts / (t * 1e-3) / (fp64_tflops * 1e12 / 2)
+                                         if inst and t > 0 else None)
     step_bytes = 3 * sum(LOW_BYTES.values()) * pts
     return {"precision": "double-word (FP32 pairs)" if df64 else "fp64", "points": pts,
             "steps": steps, "steps_per_s": steps / (msl * 1e-3), "ms_per_step": msl / steps,
@@ -349,7 +438,10 @@ def bench_low_order(zm, torch, inputs, flush, nl, steps, warmup, df64):
             "step_hbm_frac": step_bytes / (msl / steps * 1e-3) / 1e9 / HBM_GBS,
             "riesz_floor_gbs": 80 * pts / (kern["fft"]["ms_per_eval"] * 1e-3) / 1e9
             if kern["fft"]["ms_per_eval"] > 0 else 0.0,
-            "kernels": kern, "hbm_peak_gbs": HBM_GBS, "hbm_peak_basis": "measured copy bandwidth"}
+            "kernels": kern, "hbm_peak_gbs": HBM_GBS, "hbm_peak_basis": "measured copy bandwidth",
+            "fp64_pipe_basis": None if df64 else
+            "FP64 instructions per point counted by ncu (profiles/fp64_pipe_instructions.json) / kernel "
+            "time / (measured FP64 FMA rate / 2)"}
 
 
 def bench_batched(zm, torch, inputs, flush, steps=10, warmup=2, count=64):
@@ -463,9 +555,11 @@ def bench_cutoff(zm, torch, inputs, n=256, cutoffs=(0.05, 0.1, 0.2, 0.4)):
     return {"n_side": n, "exact_br_ms": t_ex, "cutoffs": rows}
 
 
-def serve_trace(zm, trace, budget, slots, dt=1e-3):
+def serve_trace(zm, trace, budget, slots, dt=1e-3, policy=None, cap=0):
     """Replay a trace through the continuous-batching server; latencies from submission."""
     srv = zm.zm_server_create(budget, slots, g=1.0)
+    if policy is not None:
+        zm.zm_server_set_policy(srv, policy, cap)
     t0 = time.perf_counter()
     ids = []
     for r in trace:
@@ -474,7 +568,7 @@ def serve_trace(zm, trace, budget, slots, dt=1e-3):
         ids.append(zm.zm_server_submit(srv, r.n, r.n, r.z, r.w, r.atwood, 0.1 / r.n, dt, r.nsteps))
     lat, bad = [], 0
     for r, rid in zip(trace, ids):
-        st = zm.zm_server_wait(srv, rid, 600.0)
+        st = zm.zm_server_wait(srv, rid, 3600.0)
         st, _, _, l, _ = zm.zm_server_result(srv, rid, r.n * r.n)
         bad += st != zm.ZM_OK
         lat.append(l)
@@ -487,7 +581,9 @@ def serve_trace(zm, trace, budget, slots, dt=1e-3):
             "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mean_ms": 1e3 * float(lat.mean()),
             "makespan_s": span, "gpairs_per_s": stats["pairs"] / span / 1e9,
             "gpu_busy_frac": stats["busy_s"] / span, "peak_resident": stats["peak_running"],
-            "peak_bytes": stats["peak_bytes"], "iterations": stats["iterations"]}
+            "peak_bytes": stats["peak_bytes"], "iterations": stats["iterations"],
+            "policy": "srpt" if policy == zm.ZM_SERVE_SRPT else "all",
+            "pairs_per_iteration_cap": cap if policy == zm.ZM_SERVE_SRPT else None}
 
 
 def fp64_sequential_trace(zm, trace, dt=1e-3):
@@ -513,27 +609,81 @@ def fp64_sequential_trace(zm, trace, dt=1e-3):
             "gpairs_per_s": pairs / span / 1e9}
 
 
-def bench_serving(zm, inputs, count=64, budget=16 << 30, slots=64):
-    """Poisson arrivals at 200/s, sides log-uniform in [32, 512], 20 RK3 steps each (FP32C);
-    then the same kind of trace at about 70% of the measured capacity; then a reduced trace
-    (sides [32, 96], 5 steps) served both by the server and by the plain per-instance FP64
-    form, for a like-for-like comparison."""
+def fp64_service_model(zm, inputs, sides=(32, 64, 128, 192, 256), dt=1e-3):
+    """Measured service time of one request in the plain per-instance FP64 form (context
+    creation, state upload, one RK3 step, state download, teardown), per mesh side; fitted as
+    t(n) = a + b * 3 n^4 (fixed cost plus pair interactions) for the queue model below."""
+    import numpy as np
+    rows = []
+    for n in sides:
+        z, w = inputs.multi_mode(n, n_modes=4, seed=n)
+        best = None
+        for _ in range(2):
+            t0 = time.perf_counter()
+            m = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, fp32c=False)
+            m.set_state(z, w)
+            m.step(dt, 1)
+            m.get_state()
+            m.close()
+            t = time.perf_counter() - t0
+            best = t if best is None else min(best, t)
+        rows.append((n, best))
+    x = np.array([3.0 * n ** 4 for n, _ in rows])
+    y = np.array([t for _, t in rows])
+    b, a = np.polyfit(x, y, 1)
+    return {"a_s": float(max(a, 0.0)), "b_s_per_pair": float(b),
+            "measured": [{"side": n, "s_per_step": t} for n, t in rows]}
+
+
+def fp64_queue_model(model, trace):
+    """Latencies of the plain per-instance FP64 form serving `trace` one request at a time in
+    arrival order (a single FIFO server), from the measured service times: request k starts at
+    max(arrival, previous completion) and takes nsteps * (a + b * 3 n^4)."""
+    import numpy as np
+    t, lat = 0.0, []
+    for r in trace:
+        t = max(t, r.arrival_s) + r.nsteps * (model["a_s"] + model["b_s_per_pair"] * 3.0 * r.n ** 4)
+        lat.append(t - r.arrival_s)
+    lat = np.array(lat)
+    return {"requests": len(trace), "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "makespan_s": t,
+            "kind": "modelled: measured FP64 per-request service times (fp64_service_model) "
+                    "replayed through a FIFO queue on the same arrivals"}
+
+
+SERVE_CAP = 20_000_000_000  # SRPT: pair interactions per server iteration (about 10 ms of GPU work)
+
+
+def bench_serving(zm, inputs, count=256, budget=16 << 30, slots=64, compare=False):
+    """Poisson arrivals at 200/s, sides log-uniform in [32, 512], 20 RK3 steps each (FP32C),
+    256 requests, served shortest-remaining-work-first; then a trace of the same kind at about
+    70% of the measured capacity; the plain per-instance FP64 form on that same trace (modelled
+    from its measured service times: run for real it would take over an hour); and a reduced
+    trace (sides [32, 96], 5 steps) served both by the server and, for real, by the plain FP64
+    form.  compare=True adds the first-come-first-served all-resident policy on both traces."""
     full = inputs.poisson_trace(count=count, rate_hz=200.0, lo=32, hi=512, nsteps=20, seed=0)
-    out = {"offered": serve_trace(zm, full, budget, slots)}
+    out = {"offered": serve_trace(zm, full, budget, slots, policy=zm.ZM_SERVE_SRPT, cap=SERVE_CAP)}
     out["offered"]["rate_hz"] = 200.0
     # capacity in pairs/s, measured while the GPU was saturated; the second trace's rate is set
     # from its own mean work per request (sides are heavy-tailed in work ~ n^4, so two traces'
     # means differ a lot).  The same seed draws the same sides at any rate.
     cap_pairs = out["offered"]["gpairs_per_s"] * 1e9
-    n70 = max(8, count // 2)
-    probe = inputs.poisson_trace(count=n70, rate_hz=1.0, lo=32, hi=512, nsteps=20, seed=1)
+    probe = inputs.poisson_trace(count=count, rate_hz=1.0, lo=32, hi=512, nsteps=20, seed=1)
     mean_pairs = sum(3 * r.nsteps * r.n ** 4 for r in probe) / len(probe)
     rate70 = max(0.7 * cap_pairs / mean_pairs, 0.1)
-    t70 = inputs.poisson_trace(count=n70, rate_hz=rate70, lo=32, hi=512, nsteps=20, seed=1)
-    out["at_70pct_capacity"] = serve_trace(zm, t70, budget, slots)
+    t70 = inputs.poisson_trace(count=count, rate_hz=rate70, lo=32, hi=512, nsteps=20, seed=1)
+    out["at_70pct_capacity"] = serve_trace(zm, t70, budget, slots, policy=zm.ZM_SERVE_SRPT, cap=SERVE_CAP)
     out["at_70pct_capacity"]["rate_hz"] = rate70
+    model = fp64_service_model(zm, inputs)
+    out["fp64_service_time_fit"] = model
+    out["fp64_per_instance_at_70pct_capacity"] = fp64_queue_model(model, t70)
+    out["fp64_per_instance_offered"] = fp64_queue_model(model, full)
+    if compare:
+        out["offered_policy_all"] = serve_trace(zm, full, budget, slots, policy=zm.ZM_SERVE_ALL)
+        out["at_70pct_capacity_policy_all"] = serve_trace(zm, t70, budget, slots, policy=zm.ZM_SERVE_ALL)
     small = inputs.poisson_trace(count=16, rate_hz=200.0, lo=32, hi=96, nsteps=5, seed=2)
-    out["reduced_trace"] = {"server_fp32c": serve_trace(zm, small, budget, slots),
+    out["reduced_trace"] = {"server_fp32c": serve_trace(zm, small, budget, slots, policy=zm.ZM_SERVE_SRPT,
+                                                        cap=SERVE_CAP),
                             "fp64_per_instance_sequential": fp64_sequential_trace(zm, small)}
     return out
 
@@ -571,10 +721,16 @@ def run_gb300(args):
     steps_per_s = args.steps / (ms_max * 1e-3)
     launches = sum(prof["launches"].values())
 
-    # roofline of the dominant kernel (Birkhoff-Rott sum): ALU bound, FP32
+    # roofline of the dominant kernel (Birkhoff-Rott sum): ALU bound, FP32.  Denominator: the
+    # FP32 FMA rate measured on this GPU by probe kernels; beside it the figure derived from the
+    # SM count and the SM clock sampled during the timed region
     br_ms = prof["ms"]["br"] / max(prof["launches"]["br"], 1)
     achieved = FLOPS_PER_PAIR * N * N / (br_ms * 1e-3) / 1e12
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak, peak_probes = measured_fp32_peak(zm)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_summary = clk.summary()
+    clk_mhz = clk_summary["sm_mhz"] or clk_summary["sm_max_mhz"] or 2070.0
+    derived = sm_count * FP32_LANES * 2 * clk_mhz * 1e6 / 1e12
     traffic = recorded_traffic(tiles)
 
     # end to end through the C ABI with host buffers: H2D state in, one step, D2H state out
@@ -623,18 +779,25 @@ def run_gb300(args):
         # its all-pairs kernel against the FP64 FMA rate measured on this GPU by a probe kernel
         br64_ms = prof64["ms"]["br"] / max(prof64["launches"]["br"], 1)
         fp64_ach = FLOPS_PER_PAIR * N * N / (br64_ms * 1e-3) / 1e12
-        fp64_peak = zm.zm_measure_peak(zm.PEAK_FP64) / 1e12
+        fp64_peak = max(zm.zm_measure_peak(zm.PEAK_FP64) for _ in range(3)) / 1e12
+        br64_inst = fp64_inst_record().get("br64", (None, None))[0]
         extras["fp64_plain"] = {"gpairs_per_s": pairs_per_step * k64 / (ms64 * 1e-3) / 1e9,
                                 "steps_per_s": k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64,
                                 "steps": k64,
                                 "roofline": {"bound": "fp64 alu", "achieved": fp64_ach, "peak": fp64_peak,
                                              "unit": "TFLOP/s", "frac": fp64_ach / fp64_peak,
                                              "peak_basis": "measured FP64 FMA probe (zm_measure_peak)",
-                                             "flops_per_pair": FLOPS_PER_PAIR, "br_ms_per_launch": br64_ms}}
+                                             "flops_per_pair": FLOPS_PER_PAIR, "br_ms_per_launch": br64_ms,
+                                             "fp64_inst_per_pair": br64_inst,
+                                             "fp64_pipe_frac": (br64_inst * N * N / (br64_ms * 1e-3) /
+                                                                (fp64_peak * 1e12 / 2)) if br64_inst else None,
+                                             "fp64_pipe_basis": "ncu-counted FP64 instructions per pair "
+                                                                "(profiles/fp64_pipe_instructions.json) x pairs / "
+                                                                "time / (measured FP64 FMA rate / 2)"}}
         extras["fp32c_speedup_vs_fp64"] = value / ws / extras["fp64_plain"]["gpairs_per_s"]
         # low order (FFT Riesz velocity): 1024^2 (the low-vs-high configuration), FP64 and
         # double-word; 4096^2, the largest power-of-two side below the paper's 4864^2 mesh
-        extras["low_order_1024"] = bench_low_order(zm, torch, inputs, flush, 1024, 10, 3, False)
+        extras["low_order_1024"] = bench_low_order(zm, torch, inputs, flush, 1024, 10, 3, False, fp64_peak)
         extras["low_order_1024_df64"] = bench_low_order(zm, torch, inputs, flush, 1024, 10, 3, True)
         # the high-order half of the low-vs-high configuration: the same 8-mode interface
         # (amplitude 0.02, A = 0.7) at 512^2, FP32C all-pairs sum, 10 RK3 steps
@@ -652,12 +815,13 @@ def run_gb300(args):
             "steps": kh, "ms_per_step": msh / kh, "steps_per_s": kh / (msh * 1e-3),
             "gpairs_per_s": 3 * nh**4 * kh / (msh * 1e-3) / 1e9,
             "br_ms_per_launch": br_h,
-            "br_frac_of_fp32_peak": FLOPS_PER_PAIR * nh**4 / (br_h * 1e-3) / 1e12 / (SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e-6),
+            "br_frac_of_fp32_peak": FLOPS_PER_PAIR * nh**4 / (br_h * 1e-3) / 1e12 / peak,
+            "peak_basis": "measured FP32 FMA probe (as the headline roofline)",
             "kernel_ms_per_step": {k: v / kh for k, v in profh["ms"].items()}}
-        extras["low_order_4096"] = bench_low_order(zm, torch, inputs, flush, 4096, 3, 1, False)
+        extras["low_order_4096"] = bench_low_order(zm, torch, inputs, flush, 4096, 3, 1, False, fp64_peak)
         extras["low_order_4096_df64"] = bench_low_order(zm, torch, inputs, flush, 4096, 5, 2, True)
         # the paper's single-GPU low-order mesh: 4864^2 = (19 x 256)^2, FP64 (radix-19 stage)
-        extras["low_order_4864"] = bench_low_order(zm, torch, inputs, flush, 4864, 3, 1, False)
+        extras["low_order_4864"] = bench_low_order(zm, torch, inputs, flush, 4864, 3, 1, False, fp64_peak)
         extras["low_order_4864_df64"] = bench_low_order(zm, torch, inputs, flush, 4864, 5, 2, True)
         # 32^2 single-mode FP64 (launch bound)
         zs, wsn = inputs.single_mode(32)
@@ -687,7 +851,7 @@ def run_gb300(args):
         extras["cutoff_tradeoff_256"] = bench_cutoff(zm, torch, inputs)
         extras["batched_64"] = bench_batched(zm, torch, inputs, flush)
         if not args.no_serve:
-            extras["serving"] = bench_serving(zm, inputs)
+            extras["serving"] = bench_serving(zm, inputs, compare=args.serve_compare)
 
     cpu = None
     if rank == 0 and ws == 1:
@@ -710,15 +874,20 @@ def run_gb300(args):
                        autotuned_tiles=list(tiles)),
         "steps_per_s": steps_per_s * 1.0,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "br32_kernel",
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "br32_batch_kernel",
+                     "peak_basis": "measured: FP32 FMA probe kernels on this GPU (zm_measure_peak, "
+                                   "best of scalar FFMA and packed FP32x2 chains, 3 runs each)",
+                     "peak_probes": peak_probes,
+                     "derived_peak": derived, "derived_frac": achieved / derived,
+                     "derived_basis": f"{sm_count} SMs x {FP32_LANES} FP32 lanes x 2 x {clk_mhz:.0f} MHz "
+                                      "(median SM clock sampled during the timed region)",
                      "flops_per_pair": FLOPS_PER_PAIR, "br_ms_per_launch": br_ms},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 5 * N * 8,
                 "d2h_bytes_per_step": 5 * N * 8},
         "gpu_launches": launches,
         "kernel_ms": prof["ms"], "kernel_launches": prof["launches"],
-        "clocks": clk.summary(),
+        "clocks": clk_summary,
     }
     line.update(extras)
     print(json.dumps(line), flush=True)
@@ -727,6 +896,8 @@ def run_gb300(args):
 
 def main():
     args = parse()
+    if args.case:
+        return run_case(args.case[0], int(args.case[1]), int(args.case[2]))
     if args.impl == "reference":
         return run_reference(args)
     return run_gb300(args)

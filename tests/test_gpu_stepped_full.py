@@ -10,7 +10,12 @@
 
 Tolerances, relative L2 per field: FP64 1e-12; FP32C 1e-6.  Besides z and w the displacement
 z - z0 is compared on its own: z itself is dominated by the mesh coordinates, while z - z0 is the
-time integral of the velocity, so it carries the velocity's relative error undiluted.
+time integral of the velocity, so it carries the velocity's relative error undiluted.  Its
+bound is the larger of the field tolerance and the rounding floor of the state: every stage
+update rounds z (|z| ~ 1) to FP64 in each code, in different operation orders, so after s steps
+(3 s roundings, a random walk) z - z0 differs by about sqrt(3 s) eps |z| per node whatever the
+velocity's accuracy; relative to |z - z0| (about 1e-4 of |z| here) that is ~3e-12 after 20
+steps.  The bound takes 2.5 sqrt(3 s) eps ||z|| / ||z - z0||.
 """
 import json
 import os
@@ -66,23 +71,24 @@ def step_on_gpu(zm, meta, z0, w0, fp32c, autotune):
     return z, w
 
 
-def compare(label, z, w, z0, zr, wr, tol):
+def compare(label, z, w, z0, zr, wr, tol, steps):
     ez, ed, ew = rel(z, zr), rel(z - z0, zr - z0), rel(w, wr)
-    print(f"{label}: rel L2 z={ez:.3e} z-z0={ed:.3e} w={ew:.3e}")
-    assert ez <= tol and ed <= tol and ew <= tol
+    floor = 2.5 * np.sqrt(3 * steps) * 2.0**-53 * np.linalg.norm(zr) / np.linalg.norm(zr - z0)
+    print(f"{label}: rel L2 z={ez:.3e} z-z0={ed:.3e} (bound {max(tol, floor):.1e}) w={ew:.3e}")
+    assert ez <= tol and ed <= max(tol, floor) and ew <= tol
 
 
 @pytest.mark.parametrize("fp32c", [True, False])
 def test_multimode_256_twenty_steps(zm, fp32c):
     meta, z0, w0, zr, wr = load_golden("multimode256_20")
     z, w = step_on_gpu(zm, meta, z0, w0, fp32c, autotune=fp32c)
-    compare(f"256^2 x 20 steps fp32c={fp32c}", z, w, z0, zr, wr, TOL32 if fp32c else TOL64)
+    compare(f"256^2 x 20 steps fp32c={fp32c}", z, w, z0, zr, wr, TOL32 if fp32c else TOL64, meta["steps"])
 
 
 def test_multimode_512_one_step_fp32c(zm):
     meta, z0, w0, zr, wr = load_golden("multimode512_1")
     z, w = step_on_gpu(zm, meta, z0, w0, True, autotune=True)
-    compare("512^2 x 1 step fp32c", z, w, z0, zr, wr, TOL32)
+    compare("512^2 x 1 step fp32c", z, w, z0, zr, wr, TOL32, meta["steps"])
 
 
 def test_low_order_1024_ten_steps():
@@ -96,4 +102,4 @@ def test_low_order_1024_ten_steps():
     model.step(1e-3, steps)
     z, w = model.get_state()
     model.close()
-    compare("low order 1024^2 x 10 steps fp64", z, w, z0, zr, wr, TOL64)
+    compare("low order 1024^2 x 10 steps fp64", z, w, z0, zr, wr, TOL64, steps)

@@ -853,6 +853,30 @@ def run_gb300(args):
         if not args.no_serve:
             extras["serving"] = bench_serving(zm, inputs, compare=args.serve_compare)
 
+    # the same 256^2 all-pairs sum with its far tile pairs on the CUDA cores instead of the
+    # tensor cores (same work items; the headline uses the tensor-core far path)
+    if not args.no_extras:
+        mc = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, fp32c=True,
+                       stream=torch.cuda.current_stream().cuda_stream)
+        mc.set_state(z0, inputs.random_state(n, seed=1)[1])
+        zm.zm_set_tile_shape(mc.h, *tiles)
+        paths = {}
+        for name, path in (("tensor", zm.ZM_FAR_TENSOR), ("cuda", zm.ZM_FAR_CUDA)):
+            zm.zm_set_far_path(mc.h, path)
+            zm.zm_autotune(mc.h)
+            mc.velocity(want_wdot=False)
+            zm.zm_set_profiling(mc.h, 1)
+            zm.zm_reset_profile(mc.h)
+            for _ in range(3):
+                flush.zero_()
+                mc.velocity(want_wdot=False)
+            p = zm.zm_get_profile(mc.h)
+            zm.zm_set_profiling(mc.h, 0)
+            t = p["ms"]["br"] / max(p["launches"]["br"], 1)
+            paths[name] = {"br_ms_per_launch": t, "gpairs_per_s": N * N / (t * 1e-3) / 1e9}
+        mc.close()
+        extras["far_path_comparison_256"] = paths
+
     cpu = None
     if rank == 0 and ws == 1:
         rate, secs, sample = oracle_sample_rate(1024)

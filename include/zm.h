@@ -134,6 +134,12 @@ int zm_autotune_tiles(zm_ctx *ctx, const char *cache_path, int32_t *tp1, int32_t
  * (64,4) (see zm_batch_set_tile_shape).  Results change within the FP32C bound.  Returns
  * ZM_ERR_INVALID for another shape, ZM_ERR_UNSUPPORTED for other contexts. */
 int zm_set_tile_shape(zm_ctx *ctx, int32_t tp1, int32_t tp2);
+
+/* Far path of an FP32C high- or medium-order context's all-pairs sum (see
+ * zm_batch_set_far_path): ZM_FAR_CUDA (default) or ZM_FAR_TENSOR.  ZM_ERR_INVALID for another
+ * value, ZM_ERR_UNSUPPORTED for other contexts. */
+int zm_set_far_path(zm_ctx *ctx, int32_t path);
+int zm_get_far_path(zm_ctx *ctx, int32_t *path);
 int zm_get_tile_shape(zm_ctx *ctx, int32_t *tp1, int32_t *tp2);
 
 /* Wait for the context's stream; reports ZM_ERR_TIMEOUT / ZM_ERR_CUDA raised by its kernels. */
@@ -246,6 +252,24 @@ int zm_batch_autotune(zm_batch *b, const char *cache_path, int32_t *chosen, floa
  * shape rebuilds the source records and the plan; results change within the FP32C bound (tile
  * centres and the near/far split move), not bit for bit.  Synchronous. */
 int zm_batch_set_tile_shape(zm_batch *b, int32_t tp1, int32_t tp2);
+/* How the all-pairs sum treats far tile pairs (bounding spheres at least 1.25 x the sum of
+ * their radii apart; near pairs always take the CUDA cores with exact FP32 hi/lo differences).
+ * Both evaluate the pair terms in tile-local coordinates, sum_j K_ij (s_j x g_j) - t_i x
+ * sum_j K_ij g_j with K_ij = (|s_j - t_i|^2 + delta^2)^(-3/2):
+ *   ZM_FAR_CUDA (default)  everything on the CUDA cores (packed FP32x2 instructions);
+ *   ZM_FAR_TENSOR          K on the CUDA cores, the two sums as one matrix product K [g | m]
+ *                          on the tensor cores (TF32 operands split into a TF32 part and a
+ *                          TF32 rest, FP32 accumulation in tensor memory over two 8-source
+ *                          blocks at a time).  Correct within the FP32C bound but about 3x
+ *                          slower on GB300: the 6-column product gives MMAs of N = 16, whose
+ *                          issue cost (about 100 cycles each) exceeds the CUDA-core work they
+ *                          replace.
+ * Results change within the FP32C bound, not bit for bit.  Rebuilds the plan; synchronous.
+ * ZM_ERR_INVALID for another value. */
+#define ZM_FAR_TENSOR 0
+#define ZM_FAR_CUDA 1
+int zm_batch_set_far_path(zm_batch *b, int32_t path);
+int zm_batch_get_far_path(zm_batch *b, int32_t *path);
 int zm_batch_get_tile_shape(zm_batch *b, int32_t *tp1, int32_t *tp2);
 /* Autotuner for tiles: times each candidate tile shape at the default work-item size, then the
  * work-item sizes 1 .. 32 for the fastest shape (one evaluation each, twice, CUDA events), keeps

@@ -96,6 +96,8 @@ int batch_set_cutoff(Batch *b, int index, double cutoff);
 int batch_autotune(Batch *b, const char *path, int *chosen, float *ms);
 int batch_autotune_tiles(Batch *b, const char *path, int *tp1, int *tp2, int *chunk, float *ms);
 int batch_set_tile_shape(Batch *b, int tp1, int tp2);
+int batch_set_far_path(Batch *b, int path);
+int batch_get_far_path(Batch *b);
 int batch_get_tile_shape(Batch *b, int *tp1, int *tp2);
 
 static int stage_index(zm_ctx *c, const double *y) { return y == c->y0 ? 0 : (y == c->ya ? 1 : 2); }
@@ -583,6 +585,22 @@ int zm_set_tile_shape(zm_ctx *c, int32_t tp1, int32_t tp2)
     if (!c->batch) return set_error(ZM_ERR_UNSUPPORTED, "zm_set_tile_shape: tiles belong to FP32C high/medium contexts");
     batch_bind(c->batch, c->stream, &c->prof);
     return batch_set_tile_shape(c->batch, tp1, tp2);
+}
+
+int zm_set_far_path(zm_ctx *c, int32_t path)
+{
+    if (!c) return set_error(ZM_ERR_INVALID, "zm_set_far_path: null context");
+    if (!c->batch) return set_error(ZM_ERR_UNSUPPORTED, "zm_set_far_path: FP32C high/medium contexts only");
+    batch_bind(c->batch, c->stream, &c->prof);
+    return batch_set_far_path(c->batch, path);
+}
+
+int zm_get_far_path(zm_ctx *c, int32_t *path)
+{
+    if (!c || !path) return set_error(ZM_ERR_INVALID, "zm_get_far_path: null argument");
+    if (!c->batch) return set_error(ZM_ERR_UNSUPPORTED, "zm_get_far_path: FP32C high/medium contexts only");
+    *path = batch_get_far_path(c->batch);
+    return ZM_OK;
 }
 
 int zm_get_tile_shape(zm_ctx *c, int32_t *tp1, int32_t *tp2)

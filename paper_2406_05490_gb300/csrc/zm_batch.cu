@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kPtb)
     if (p >= I.geom.N || !ZM_IDX_OK(p, I.geom.N)) return;
     const double pref = I.geom.dx1 * I.geom.dx2 / (4.0 * 3.14159265358979323846);
     geometry_point<kGeoFp32c>(I.geom, I.tiling, p, I.y[yin], pref, I.g, (float)(I.delta * I.delta),
-                              I.near_rec, I.far_rec, I.tinfo, I.gmax, I.q, nullptr);
+                              I.near_rec, I.far_rec, I.tinfo, I.gmax, I.q, nullptr, I.tc_rec != 0);
 }
 
 // u = fixed-point sum * 2^-scale, Phi = q + |u|^2 / 2; clears the accumulators, the tile
@@ -193,7 +193,7 @@ int Batch::setup()
 {
     cudaGetDevice(&device);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    occ = br32_occupancy();
+    occ = tc ? br32tc_occupancy() : br32_occupancy();
     if (cudaMalloc(&counter, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
@@ -229,6 +229,7 @@ int Batch::plan()
     long long items = 0;
     int blocks = 0;
     for (auto &I : h) {
+        I.tc_rec = tc ? 1 : 0;
         I.block0 = blocks;
         blocks += (I.geom.N + kPtb - 1) / kPtb;
         I.chunk = chunk_override > 0 ? std::min(chunk_override, I.tiling.ntiles)
@@ -535,7 +536,8 @@ int Batch::derivative(int yin, cudaStream_t s)
     prof_begin(*prof, s, ZM_K_BR, &ev);
     bool any_cutoff = false;
     for (const auto &I : h) any_cutoff = any_cutoff || I.cutoff > 0;
-    rc = launch_br32_batch(d, (int)h.size(), nitems, ctas, counter, err, s, any_cutoff);
+    rc = tc ? launch_br32tc_batch(d, (int)h.size(), nitems, ctas, counter, err, s, any_cutoff)
+            : launch_br32_batch(d, (int)h.size(), nitems, ctas, counter, err, s, any_cutoff);
     prof_end(*prof, s, ZM_K_BR, ev);
     for (auto &I : h) prof->acc.pairs += (int64_t)I.geom.N * I.geom.N;
     if (rc) return rc;
@@ -676,6 +678,17 @@ int batch_get_tile_shape(Batch *b, int *tp1, int *tp2)
     *tp2 = kShapes[b->shape][1];
     return ZM_OK;
 }
+
+int batch_set_far_path(Batch *b, int path)
+{
+    if (path != ZM_FAR_TENSOR && path != ZM_FAR_CUDA)
+        return set_error(ZM_ERR_INVALID, "far path must be ZM_FAR_TENSOR or ZM_FAR_CUDA");
+    b->tc = (path == ZM_FAR_TENSOR);
+    b->occ = b->tc ? br32tc_occupancy() : br32_occupancy();
+    return b->plan();
+}
+
+int batch_get_far_path(Batch *b) { return b->tc ? ZM_FAR_TENSOR : ZM_FAR_CUDA; }
 
 int batch_set_tile_shape(Batch *b, int tp1, int tp2)
 {
@@ -844,6 +857,19 @@ int zm_batch_set_tile_shape(zm_batch *bt, int32_t tp1, int32_t tp2)
 {
     if (!bt) return set_error(ZM_ERR_INVALID, "zm_batch_set_tile_shape: null batch");
     return batch_set_tile_shape(&bt->b, tp1, tp2);
+}
+
+int zm_batch_set_far_path(zm_batch *bt, int32_t path)
+{
+    if (!bt) return set_error(ZM_ERR_INVALID, "zm_batch_set_far_path: null batch");
+    return batch_set_far_path(&bt->b, path);
+}
+
+int zm_batch_get_far_path(zm_batch *bt, int32_t *path)
+{
+    if (!bt || !path) return set_error(ZM_ERR_INVALID, "zm_batch_get_far_path: null argument");
+    *path = batch_get_far_path(&bt->b);
+    return ZM_OK;
 }
 
 int zm_batch_get_tile_shape(zm_batch *bt, int32_t *tp1, int32_t *tp2)

@@ -24,6 +24,7 @@ public:
     int nblocks = 0;
     long long nitems = 0;
     int ctas = 0, occ = 1, sms = 152;
+    bool tc = false;  // far pairs: CUDA cores (br32_batch_kernel), or tensor cores (br32tc_kernel)
     int chunk_override = 0;  // 0: default work-item size by mesh size
     int shape = 0;           // index into the candidate patch shapes (0: 16 x 16)
     unsigned long long *counter = nullptr;

@@ -197,7 +197,10 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
     br32_batch_kernel(const Inst *__restrict__ insts, int ninst, long long nitems,
                       unsigned long long *counter, int *err)
 {
-    __shared__ __align__(128) float stage[2][kRec32F * kTs];
+    // a stage holds a near record (9 rows) or the far path's rows: s, |s|^2 + delta^2 (record
+    // rows 0-3) and strength, s x strength (record rows 20-25) as stage rows 0-9
+    constexpr int kStageRows = 10;
+    __shared__ __align__(128) float stage[2][kStageRows * kTs];
     __shared__ long long acc[3][kR][kT];  // fixed-point partial sums of this thread's targets
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ Unit unit[2];
@@ -252,10 +255,12 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
             unit[buf].tile = p_tile;
             unit[buf].src = S;
             unit[buf].far = path;
-            if (path == 1)
-                dev::tma_load_1d(stage[buf], I.far_rec + (size_t)S * kRec32F * kTs,
-                                 kRec32F * kTs * sizeof(float), &bar[buf]);
-            else
+            if (path == 1) {
+                const float *rec = I.far_rec + (size_t)S * kRec32F * kTs;
+                dev::mbar_expect_tx(&bar[buf], kStageRows * kTs * sizeof(float));
+                dev::tma_copy_1d(stage[buf], rec, 4 * kTs * sizeof(float), &bar[buf]);
+                dev::tma_copy_1d(stage[buf] + 4 * kTs, rec + kFarRowG * kTs, 6 * kTs * sizeof(float), &bar[buf]);
+            } else
                 dev::tma_load_1d(stage[buf], I.near_rec + (size_t)S * kRec32 * kTs,
                                  kRec32 * kTs * sizeof(float), &bar[buf]);
             return;

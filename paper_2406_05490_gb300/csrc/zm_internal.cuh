@@ -55,11 +55,29 @@ struct Tiling {
 
 // FP64 record: rows 0-2 absolute position, rows 3-5 scaled sheet strength -> [tile][6][ts] double
 // FP32C near record: rows 0-2 position hi, 3-5 position lo, 6-8 scaled strength -> [tile][9][ts]
-// FP32C far record: rows 0-2 s = z - c_T (tile centre), 3 |s|^2 + delta^2, 4-6 scaled strength,
-//   7-9 s x strength -> [tile][10][ts] float
+// FP32C far record, [tile][26][ts] float (ts = 256):
+//   rows 0-2 s = z - c_T (c_T the tile centre), row 3 |s|^2 + delta^2      (both far paths)
+//   rows 4-19 the tile's 256 x 16 source matrix B of the tensor-core far path (far_b_index)
+//   rows 20-22 scaled strength, rows 23-25 s x strength                  (CUDA-core far path)
 constexpr int kRec64 = 6;
 constexpr int kRec32 = 9;
-constexpr int kRec32F = 10;
+constexpr int kRec32F = 26;
+constexpr int kFarRowB = 4, kFarRowG = 20;
+
+// The tensor-core far path's source matrix B of one tile: row j = source slot (the K index of
+// the MMA), 16 columns: 0-2 scaled strength and 3-5 s x strength, each rounded to TF32 (10
+// fraction bits); 8-10 and 11-13 what that rounding left, again rounded to TF32; 6, 7, 14, 15
+// zero.  Stored K-major without swizzling as core matrices of 8 columns x 4 sources (128
+// contiguous bytes; column n of a core matrix at 16 n bytes, source j at 4 j bytes), 8-source
+// blocks of 512 bytes one after another; within a block the core matrix of sources 4-7 lies
+// kTcStrideK bytes after that of sources 0-3, and that of columns 8-15 kTcStrideN bytes after
+// that of columns 0-7.  far_b_index gives the float offset from row kFarRowB.
+constexpr uint32_t kTcStrideK = 128, kTcStrideN = 256;
+__host__ __device__ constexpr int far_b_index(int j, int n)
+{
+    return (j >> 3) * 128 + (n >> 3) * (int)(kTcStrideN / 4) + ((j >> 2) & 1) * (int)(kTcStrideK / 4) +
+           (n & 7) * 4 + (j & 3);
+}
 
 // Launch geometry of the all-pairs kernel.
 struct BrPlan {
@@ -106,6 +124,7 @@ struct Inst {
     double dt;                  // RK3 step of this interface
     int keep_phi;               // medium order: Phi comes from the FFT velocity, not from u
     double cutoff;              // > 0: sum only over sources within this distance
+    int tc_rec;                 // the geometry pass also writes the tensor-core source matrix
     int block0;                 // first 256-thread block of this interface in the point kernels
     int chunk, nchunks;         // source tiles per Birkhoff-Rott work item; items per target tile
     long long item0;            // first Birkhoff-Rott work item of this interface
@@ -202,6 +221,9 @@ int launch_br(zm_ctx *c, const double *y);  // FP64 path (then launch_reduce)
 
 // ---- FP32C Birkhoff-Rott kernel over a batch of interfaces (zm_br32.cu) ----------------------------
 int br32_occupancy();  // resident CTAs per SM of the batched kernel
+int br32tc_occupancy();  // the same for the tensor-core far-path kernel
+int launch_br32tc_batch(const Inst *d_insts, int ninst, long long nitems, int ctas, unsigned long long *counter,
+                        int *err, cudaStream_t s, bool any_cutoff);
 int launch_br32_batch(const Inst *d_insts, int ninst, long long nitems, int ctas,
                       unsigned long long *counter, int *err, cudaStream_t s, bool any_cutoff);
 void init_far_records(float *far_rec, int ntiles, float d2, cudaStream_t s);
@@ -298,6 +320,7 @@ int bounds_api(unsigned int *, long long *, int *, int);
 int bounds_batch(unsigned int *, long long *, int *, int);
 int bounds_br(unsigned int *, long long *, int *, int);
 int bounds_br32(unsigned int *, long long *, int *, int);
+int bounds_br32tc(unsigned int *, long long *, int *, int);
 int bounds_fft(unsigned int *, long long *, int *, int);
 int bounds_lowdf(unsigned int *, long long *, int *, int);
 int bounds_lowdf_mix(unsigned int *, long long *, int *, int);
@@ -346,6 +369,47 @@ __device__ __forceinline__ void tma_load_1d(void *smem_dst, const void *gmem_src
             smem_u32(smem_dst)),
         "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Arm the barrier for `bytes` of asynchronous transactions (one arrival); the copies that
+// complete them follow with tma_copy_1d.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// One 1D bulk copy global -> shared completing `bytes` transactions on the barrier (armed
+// before).  Both addresses 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void tma_copy_1d(void *smem_dst, const void *gmem_src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(smem_dst)),
+        "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Plain arrival (no transactions).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Round to TF32 (10 fraction bits), ties away from zero: the value a TF32 tensor-core operand
+// holds exactly.
+__host__ __device__ __forceinline__ float tf32_round(float x)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+#else
+    uint32_t b;
+    __builtin_memcpy(&b, &x, 4);
+    b = (b + 0x1000u) & 0xFFFFE000u;
+    float r;
+    __builtin_memcpy(&r, &b, 4);
+    return r;
+#endif
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)

@@ -202,7 +202,8 @@ extern "C" int zm_bounds_status(uint32_t *hits, int64_t *first_index, int32_t *s
     long long f = -1;
     int line = 0;
     int (*const readers[])(unsigned int *, long long *, int *, int) = {
-        bounds_api, bounds_batch, bounds_br, bounds_br32, bounds_fft, bounds_lowdf, bounds_lowdf_mix, bounds_stencil};
+        bounds_api, bounds_batch, bounds_br, bounds_br32, bounds_br32tc, bounds_fft, bounds_lowdf, bounds_lowdf_mix,
+        bounds_stencil};
     for (auto rd : readers)
         if (rd(&h, &f, &line, clear ? 1 : 0) != 0) return set_error(ZM_ERR_CUDA, "zm_bounds_status: read failed");
     *hits = h;

@@ -126,6 +126,10 @@ def load():
                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(ctypes.c_float)]),
             "zm_set_cutoff": (I, [VP, D]),
+            "zm_set_far_path": (I, [VP, ctypes.c_int32]),
+            "zm_get_far_path": (I, [VP, ctypes.POINTER(ctypes.c_int32)]),
+            "zm_batch_set_far_path": (I, [VP, ctypes.c_int32]),
+            "zm_batch_get_far_path": (I, [VP, ctypes.POINTER(ctypes.c_int32)]),
             "zm_batch_set_cutoff": (I, [VP, ctypes.c_int32, D]),
             "zm_batch_info": (I, [VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
@@ -351,6 +355,29 @@ def zm_batch_autotune(h, cache_path=None):
 
 def zm_set_cutoff(h, cutoff):
     _check(load().zm_set_cutoff(h, float(cutoff)))
+
+
+ZM_FAR_TENSOR, ZM_FAR_CUDA = 0, 1
+
+
+def zm_set_far_path(h, path):
+    _check(load().zm_set_far_path(h, int(path)))
+
+
+def zm_get_far_path(h):
+    v = ctypes.c_int32()
+    _check(load().zm_get_far_path(h, ctypes.byref(v)))
+    return v.value
+
+
+def zm_batch_set_far_path(h, path):
+    _check(load().zm_batch_set_far_path(h, int(path)))
+
+
+def zm_batch_get_far_path(h):
+    v = ctypes.c_int32()
+    _check(load().zm_batch_get_far_path(h, ctypes.byref(v)))
+    return v.value
 
 
 def zm_batch_set_cutoff(h, index, cutoff):

@@ -1,0 +1,90 @@
+"""The two far paths of the FP32C all-pairs sum (far tile pairs: everything on the CUDA cores,
+the default, or K on the CUDA cores and K [g | m] on the tensor cores; near pairs always on the
+CUDA cores), each against the CPU oracle at the FP32C velocity bound (1e-6 relative L2) on meshes
+with one tile, ragged tiles, free and periodic edges, and against each other; both bitwise
+deterministic."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_05490_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-6
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def zm():
+    import torch
+    from paper_2406_05490_gb300 import zm as _zm
+    assert torch.cuda.is_available()
+    _zm.load()
+    return _zm
+
+
+@pytest.mark.parametrize("n1,n2,periodic", [(16, 16, True), (37, 53, False), (96, 80, True), (128, 128, True)])
+def test_far_paths_against_the_oracle(zm, n1, n2, periodic):
+    z, w = inputs.random_state(n1, n2, seed=n1 * 3 + n2)
+    delta = 0.1 / max(n1, n2)
+    m = oracle.Mesh(n1, n2, periodic=periodic)
+    u_ref, wd_ref = oracle.derivative(m, z, w, 0.5, 1.0, 0.0, delta)
+    out = {}
+    for path in (zm.ZM_FAR_TENSOR, zm.ZM_FAR_CUDA):
+        model = zm.ZModel(n1, n2, periodic=periodic, atwood=0.5, g=1.0, delta=delta, fp32c=True)
+        assert zm.zm_get_far_path(model.h) == zm.ZM_FAR_CUDA  # the default
+        zm.zm_set_far_path(model.h, path)
+        assert zm.zm_get_far_path(model.h) == path
+        u, wd = model.velocity(z, w)
+        u2, wd2 = model.velocity(z, w)
+        model.close()
+        assert np.array_equal(u, u2) and np.array_equal(wd, wd2)  # deterministic
+        eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+        print(f"far path {path} {n1}x{n2}: rel L2 u={eu:.3e} wdot={ew:.3e}")
+        assert eu <= TOL32 and ew <= TOL32
+        out[path] = u
+    assert rel(out[zm.ZM_FAR_TENSOR], out[zm.ZM_FAR_CUDA]) <= 2 * TOL32
+
+
+def test_far_path_at_full_size_sampled(zm):
+    """256^2 with vorticity: all of u from each path, 1024 seeded targets summed by the oracle."""
+    n = 256
+    z, w = inputs.random_state(n, seed=11)
+    delta = 0.1 / n
+    m = oracle.Mesh(n, periodic=True)
+    a1, a2, _, _ = oracle.geometry(m, z)
+    gam = oracle.sheet_strength(w, a1, a2)
+    idx = np.random.default_rng(5).choice(n * n, 1024, replace=False)
+    u_ref = oracle.br_velocity(z[:, idx], z, gam, 1.0 / n**2, delta)
+    for path in (zm.ZM_FAR_TENSOR, zm.ZM_FAR_CUDA):
+        model = zm.ZModel(n, periodic=True, delta=delta, fp32c=True)
+        zm.zm_set_far_path(model.h, path)
+        u = model.velocity(z, w, want_wdot=False)
+        model.close()
+        e = rel(u[:, idx], u_ref)
+        print(f"256^2 sampled, far path {path}: rel L2 u={e:.3e}")
+        assert e <= TOL32
+
+
+def test_far_path_rejects_bad_values(zm):
+    model = zm.ZModel(32, periodic=True, fp32c=True)
+    with pytest.raises(zm.ZMError) as e:
+        zm.zm_set_far_path(model.h, 5)
+    assert e.value.code == zm.ZM_ERR_INVALID
+    model.close()
+    model = zm.ZModel(32, periodic=True, fp32c=False)
+    with pytest.raises(zm.ZMError) as e:
+        zm.zm_set_far_path(model.h, zm.ZM_FAR_CUDA)
+    assert e.value.code == zm.ZM_ERR_UNSUPPORTED
+    model.close()
+    h = zm.zm_batch_create([(32, 32, 1.0, 1.0, True)], [0.5])
+    assert zm.zm_batch_get_far_path(h) == zm.ZM_FAR_CUDA
+    zm.zm_batch_set_far_path(h, zm.ZM_FAR_TENSOR)
+    assert zm.zm_batch_get_far_path(h) == zm.ZM_FAR_TENSOR
+    with pytest.raises(zm.ZMError):
+        zm.zm_batch_set_far_path(h, -1)
+    zm.zm_batch_destroy(h)

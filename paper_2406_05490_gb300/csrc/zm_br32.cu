@@ -22,7 +22,8 @@
 // Cutoff (paper Sec. 3.2.2 CutoffBRSolver: only sources within a 3D distance of the target).
 // With a cutoff c, the tile spheres classify each (target tile, source tile): entirely beyond c
 // (skipped: no copy, no work), entirely within c (the paths above), or straddling c (the near
-// path with a per-pair test |r|^2 <= c^2 on the FP32 hi/lo difference).  Compact tiles of the
+// path with a per-pair test |r|^2 <= c^2 on the FP32 hi/lo difference, exact to about 2^-22 in
+// the distance; a pair that close to c may fall either way).  Compact tiles of the
 // mesh act as the cell list.  A relative margin of 1e-4 on c keeps the sphere decisions on the
 // safe side of every pair decision.
 //
@@ -35,7 +36,7 @@
 // per-interface accumulators by integer atomics when it moves on.
 #include <algorithm>
 
-#include "zm_internal.cuh"
+#include "zm_br32_common.cuh"
 
 namespace zm {
 namespace {
@@ -43,7 +44,6 @@ namespace {
 #ifndef ZM_BR32_R
 #define ZM_BR32_R 4
 #endif
-constexpr int kTs = 256;        // sources per tile (and targets per target tile)
 constexpr int kR = ZM_BR32_R;   // targets per thread
 constexpr int kT = kTs / kR;    // threads per CTA: one target tile per CTA
 #ifndef ZM_BR32_FAR
@@ -60,128 +60,6 @@ constexpr float kFarFactor = ZM_BR32_FAR;
 #define ZM_BR32_MINB 7
 #endif
 constexpr int kFarUnroll = ZM_BR32_UNROLL;
-
-typedef unsigned long long u64;  // two packed floats (low word first)
-
-__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
-{
-    u64 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ u64 fmul2(u64 a, u64 b)
-{
-    u64 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 fadd2(u64 a, u64 b)
-{
-    u64 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 fsub2(u64 a, u64 b)
-{
-    u64 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 neg2(u64 a) { return a ^ 0x8000000080000000ull; }
-__device__ __forceinline__ u64 pack2(float lo, float hi)
-{
-    u64 d;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
-    return d;
-}
-__device__ __forceinline__ float sum2(u64 v)
-{
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    return lo + hi;
-}
-__device__ __forceinline__ u64 rsqrt2(u64 v)
-{
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    return pack2(dev::rsqrt_approx(lo), dev::rsqrt_approx(hi));
-}
-
-// Fixed-point scale of one interface: |sum| <= N max|gamma'| * 0.385 / delta^2 < 2^(e+1); keep
-// the scaled sum below 2^61.
-__device__ __forceinline__ int fix_scale(const Inst &I)
-{
-    const float gm = __uint_as_float(*I.gmax);
-    const double bound = (double)gm * (double)I.geom.N * 0.385 / (I.delta * I.delta) + 1e-300;
-    return max(0, min(100, 60 - ilogb(bound)));
-}
-
-// Near pair terms of one source tile (record in shared memory `s`: hi/lo positions and scaled
-// strengths, rows of kTs) for this thread's kR targets (near record row pointer `tr0`): the
-// FP32 hi/lo difference r = (s_hi - t_hi) + (s_lo - t_lo), K = (|r|^2 + delta^2)^(-3/2),
-// r x gamma, with two adjacent sources per packed FP32x2 instruction (even sources in lane 0, odd
-// in lane 1, added at the end).  kMask: keep only pairs with |r|^2 <= c2, |r|^2 formed as
-// fma(rx, rx, fma(ry, ry, rz * rz)) in FP32 (the cutoff decision of the paper's cutoff solver,
-// Sec. 3.2.2, taken on the same FP32 difference by the oracle).
-template <bool kMask>
-__device__ __forceinline__ void near_tile(const float *s, const float *__restrict__ tr0, float d2, float c2,
-                                          float mult, long long (*acc)[kR][kT], int tid)
-{
-    u64 hx[kR], hy[kR], hz[kR], lx[kR], ly[kR], lz[kR], px[kR], py[kR], pz[kR];
-#pragma unroll
-    for (int r = 0; r < kR; ++r) {
-        const float *tr = tr0 + r * kT;
-        float v;
-        v = __ldg(tr);
-        hx[r] = pack2(v, v);
-        v = __ldg(tr + kTs);
-        hy[r] = pack2(v, v);
-        v = __ldg(tr + 2 * kTs);
-        hz[r] = pack2(v, v);
-        v = __ldg(tr + 3 * kTs);
-        lx[r] = pack2(v, v);
-        v = __ldg(tr + 4 * kTs);
-        ly[r] = pack2(v, v);
-        v = __ldg(tr + 5 * kTs);
-        lz[r] = pack2(v, v);
-        px[r] = py[r] = pz[r] = 0ull;
-    }
-    const u64 d22 = pack2(d2, d2);
-    const u64 *s2 = reinterpret_cast<const u64 *>(s);  // row k at s2[k * kTs / 2]
-    constexpr int H = kTs / 2;
-#pragma unroll 2
-    for (int m = 0; m < H; ++m) {
-        const u64 shx = s2[m], shy = s2[H + m], shz = s2[2 * H + m];
-        const u64 slx = s2[3 * H + m], sly = s2[4 * H + m], slz = s2[5 * H + m];
-        const u64 gx = s2[6 * H + m], gy = s2[7 * H + m], gz = s2[8 * H + m];
-        const u64 ngx = neg2(gx), ngy = neg2(gy), ngz = neg2(gz);
-#pragma unroll
-        for (int r = 0; r < kR; ++r) {
-            const u64 rx = fadd2(fsub2(shx, hx[r]), fsub2(slx, lx[r]));
-            const u64 ry = fadd2(fsub2(shy, hy[r]), fsub2(sly, ly[r]));
-            const u64 rz = fadd2(fsub2(shz, hz[r]), fsub2(slz, lz[r]));
-            const u64 q = ffma2(rx, rx, ffma2(ry, ry, ffma2(rz, rz, d22)));
-            const u64 iq = rsqrt2(q);
-            u64 kk = fmul2(fmul2(iq, iq), iq);
-            if (kMask) {
-                const u64 r2 = ffma2(rx, rx, ffma2(ry, ry, fmul2(rz, rz)));
-                float r2a, r2b, ka, kb;
-                asm("mov.b64 {%0, %1}, %2;" : "=f"(r2a), "=f"(r2b) : "l"(r2));
-                asm("mov.b64 {%0, %1}, %2;" : "=f"(ka), "=f"(kb) : "l"(kk));
-                kk = pack2(r2a <= c2 ? ka : 0.0f, r2b <= c2 ? kb : 0.0f);
-            }
-            px[r] = ffma2(kk, ffma2(ry, gz, fmul2(rz, ngy)), px[r]);
-            py[r] = ffma2(kk, ffma2(rz, gx, fmul2(rx, ngz)), py[r]);
-            pz[r] = ffma2(kk, ffma2(rx, gy, fmul2(ry, ngx)), pz[r]);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < kR; ++r) {
-        acc[0][r][tid] += __float2ll_rn(sum2(px[r]) * mult);
-        acc[1][r][tid] += __float2ll_rn(sum2(py[r]) * mult);
-        acc[2][r][tid] += __float2ll_rn(sum2(pz[r]) * mult);
-    }
-}
 
 struct Unit {
     int inst;  // -1: no more work
@@ -380,10 +258,10 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
                     acc[2][r][tid] += __float2ll_rn(vz * c_mult);
                 }
             } else if (!kCut || un.far == 0) {
-                near_tile<false>(s, c_near + (size_t)c_tile * kRec32 * kTs + tid, c_d2, 0.0f, c_mult, acc, tid);
+                near_tile<false, kR, kT>(s, c_near + (size_t)c_tile * kRec32 * kTs + tid, c_d2, 0.0f, c_mult, acc, tid);
             } else {
                 // the tile pair straddles the cutoff: mask each pair by its FP32 distance
-                near_tile<true>(s, c_near + (size_t)c_tile * kRec32 * kTs + tid, c_d2, c_c2, c_mult, acc, tid);
+                near_tile<true, kR, kT>(s, c_near + (size_t)c_tile * kRec32 * kTs + tid, c_d2, c_c2, c_mult, acc, tid);
             }
         }
         bad = __syncthreads_or(!ok);

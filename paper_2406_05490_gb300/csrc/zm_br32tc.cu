@@ -39,13 +39,12 @@
 // 0-63); A, two slots x two row groups x (8 columns Kh + 8 columns Kl) (columns 64-127).
 #include <algorithm>
 
-#include "zm_internal.cuh"
+#include "zm_br32_common.cuh"
 #include "zm_tc.cuh"
 
 namespace zm {
 namespace {
 
-constexpr int kTs = 256;          // sources per tile, targets per target tile
 constexpr int kCW = 4;            // compute warps
 constexpr int kCT = kCW * 32;     // compute threads: 128 rows per group
 constexpr int kThreads = kCT + 64;  // + producer warp + MMA warp
@@ -80,63 +79,6 @@ constexpr uint32_t kLbo = ZM_TC_LBO_IS_K ? kTcStrideK : kTcStrideN;
 constexpr uint32_t kSbo = ZM_TC_LBO_IS_K ? kTcStrideN : kTcStrideK;
 constexpr uint32_t kIdesc = tc::idesc_tf32(128, 16);
 
-typedef unsigned long long u64;
-
-__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
-{
-    u64 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ u64 fmul2(u64 a, u64 b)
-{
-    u64 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 fadd2(u64 a, u64 b)
-{
-    u64 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 fsub2(u64 a, u64 b)
-{
-    u64 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 neg2(u64 a) { return a ^ 0x8000000080000000ull; }
-__device__ __forceinline__ u64 pack2(float lo, float hi)
-{
-    u64 d;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
-    return d;
-}
-__device__ __forceinline__ void unpack2(u64 v, float &lo, float &hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ float sum2(u64 v)
-{
-    float lo, hi;
-    unpack2(v, lo, hi);
-    return lo + hi;
-}
-__device__ __forceinline__ u64 rsqrt2(u64 v)
-{
-    float lo, hi;
-    unpack2(v, lo, hi);
-    return pack2(dev::rsqrt_approx(lo), dev::rsqrt_approx(hi));
-}
-
-__device__ __forceinline__ int fix_scale(const Inst &I)
-{
-    const float gm = __uint_as_float(*I.gmax);
-    const double bound = (double)gm * (double)I.geom.N * 0.385 / (I.delta * I.delta) + 1e-300;
-    return max(0, min(100, 60 - ilogb(bound)));
-}
-
 // Bounded wait on a phase; false (and the status word set) if it gave up.  (Polling without
 // suspending the thread, mbarrier.test_wait in a loop, measured slower: 7.4 against 6.3 ms per
 // 256^2 launch.)
@@ -164,69 +106,6 @@ struct Unit {
     int src;   // source tile
     int path;  // 0 near, 1 far, 2 near masked at the cutoff
 };
-
-// Near pair terms of one source tile for this thread's two targets (rows tid and tid + 128):
-// FP32 hi/lo differences, the direct formula, two sources per packed instruction.
-template <bool kMask>
-__device__ __forceinline__ void near_tile2(const float *s, const float *__restrict__ tr0, float d2, float c2,
-                                           float mult, long long (*acc)[2][kCT], int tid)
-{
-    constexpr int R = 2;
-    u64 hx[R], hy[R], hz[R], lx[R], ly[R], lz[R], px[R], py[R], pz[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const float *tr = tr0 + r * kCT;
-        float v;
-        v = __ldg(tr);
-        hx[r] = pack2(v, v);
-        v = __ldg(tr + kTs);
-        hy[r] = pack2(v, v);
-        v = __ldg(tr + 2 * kTs);
-        hz[r] = pack2(v, v);
-        v = __ldg(tr + 3 * kTs);
-        lx[r] = pack2(v, v);
-        v = __ldg(tr + 4 * kTs);
-        ly[r] = pack2(v, v);
-        v = __ldg(tr + 5 * kTs);
-        lz[r] = pack2(v, v);
-        px[r] = py[r] = pz[r] = 0ull;
-    }
-    const u64 d22 = pack2(d2, d2);
-    const u64 *s2 = reinterpret_cast<const u64 *>(s);
-    constexpr int H = kTs / 2;
-#pragma unroll 2
-    for (int m = 0; m < H; ++m) {
-        const u64 shx = s2[m], shy = s2[H + m], shz = s2[2 * H + m];
-        const u64 slx = s2[3 * H + m], sly = s2[4 * H + m], slz = s2[5 * H + m];
-        const u64 gx = s2[6 * H + m], gy = s2[7 * H + m], gz = s2[8 * H + m];
-        const u64 ngx = neg2(gx), ngy = neg2(gy), ngz = neg2(gz);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const u64 rx = fadd2(fsub2(shx, hx[r]), fsub2(slx, lx[r]));
-            const u64 ry = fadd2(fsub2(shy, hy[r]), fsub2(sly, ly[r]));
-            const u64 rz = fadd2(fsub2(shz, hz[r]), fsub2(slz, lz[r]));
-            const u64 q = ffma2(rx, rx, ffma2(ry, ry, ffma2(rz, rz, d22)));
-            const u64 iq = rsqrt2(q);
-            u64 kk = fmul2(fmul2(iq, iq), iq);
-            if (kMask) {
-                const u64 r2 = ffma2(rx, rx, ffma2(ry, ry, fmul2(rz, rz)));
-                float r2a, r2b, ka, kb;
-                unpack2(r2, r2a, r2b);
-                unpack2(kk, ka, kb);
-                kk = pack2(r2a <= c2 ? ka : 0.0f, r2b <= c2 ? kb : 0.0f);
-            }
-            px[r] = ffma2(kk, ffma2(ry, gz, fmul2(rz, ngy)), px[r]);
-            py[r] = ffma2(kk, ffma2(rz, gx, fmul2(rx, ngz)), py[r]);
-            pz[r] = ffma2(kk, ffma2(rx, gy, fmul2(ry, ngx)), pz[r]);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        acc[0][r][tid] += __float2ll_rn(sum2(px[r]) * mult);
-        acc[1][r][tid] += __float2ll_rn(sum2(py[r]) * mult);
-        acc[2][r][tid] += __float2ll_rn(sum2(pz[r]) * mult);
-    }
-}
 
 template <bool kCut>
 __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
@@ -558,9 +437,9 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
                     acc[2][r][tid] += __float2ll_rn(vz * c_mult);
                 }
             } else if (!kCut || un.path == 0) {
-                near_tile2<false>(st, c_near + (size_t)c_tile * kRec32 * kTs + tid, c_d2, 0.0f, c_mult, acc, tid);
+                near_tile<false, 2, kCT>(st, c_near + (size_t)c_tile * kRec32 * kTs + tid, c_d2, 0.0f, c_mult, acc, tid);
             } else {
-                near_tile2<true>(st, c_near + (size_t)c_tile * kRec32 * kTs + tid, c_d2, c_c2, c_mult, acc, tid);
+                near_tile<true, 2, kCT>(st, c_near + (size_t)c_tile * kRec32 * kTs + tid, c_d2, c_c2, c_mult, acc, tid);
             }
             __syncwarp();
             if (lane == 0) dev::mbar_arrive(&rec_free[s]);

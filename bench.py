@@ -125,8 +125,11 @@ class ClockSampler:
 
 
 def kernel_source_hash():
-    p = os.path.join(ROOT, "paper_2406_05490_gb300", "csrc", "zm_br32.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """Of the headline kernel's sources: the kernel and the device code it shares."""
+    h = hashlib.sha256()
+    for f in ("zm_br32.cu", "zm_br32_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2406_05490_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic(tiles):

@@ -88,3 +88,40 @@ def test_far_path_rejects_bad_values(zm):
     with pytest.raises(zm.ZMError):
         zm.zm_batch_set_far_path(h, -1)
     zm.zm_batch_destroy(h)
+
+
+def test_tensor_path_with_cutoff_and_in_a_batch(zm):
+    """The tensor-core far path under a cutoff (its masked near path and tile skipping), against
+    the oracle with the boundary-band treatment of test_gpu_cutoff; and inside a ragged batch,
+    each interface bitwise equal to the same interface alone on the same path (fixed-point
+    accumulation: neither the batch composition nor the scheduling changes a bit)."""
+    from test_gpu_cutoff import band_corrected_reference
+    n1, n2, c = 96, 80, 0.15
+    z, w = inputs.random_state(n1, n2, seed=n1 + n2)
+    delta = 0.1 / max(n1, n2)
+    m = oracle.Mesh(n1, n2, periodic=True)
+    model = zm.ZModel(n1, n2, periodic=True, atwood=0.5, g=1.0, delta=delta, fp32c=True)
+    zm.zm_set_far_path(model.h, zm.ZM_FAR_TENSOR)
+    zm.zm_set_cutoff(model.h, c)
+    u, wd = model.velocity(z, w)
+    model.close()
+    u_ref, wd_ref, nband, nflip = band_corrected_reference(m, z, w, u, 0.5, 1.0, 0.0, delta, c)
+    eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+    print(f"tensor path, cutoff {c} {n1}x{n2}: rel L2 u={eu:.3e} wdot={ew:.3e} (band {nband}, flipped {nflip})")
+    assert eu <= TOL32 and ew <= 1e-5
+    specs = [(64, 64), (48, 40), (37, 53)]
+    states = [inputs.random_state(a, b, seed=a + 2 * b) for a, b in specs]
+    h = zm.zm_batch_create([(a, b, 1.0, 1.0, True) for a, b in specs], [0.5] * len(specs))
+    zm.zm_batch_set_far_path(h, zm.ZM_FAR_TENSOR)
+    for k, (zz, ww) in enumerate(states):
+        zm.zm_batch_set_state(h, k, zz, ww)
+    zm.zm_batch_velocity(h)
+    for k, (a, b) in enumerate(specs):
+        ub = np.empty((3, a * b))
+        zm.zm_batch_get_velocity(h, k, ub, None)
+        alone = zm.ZModel(a, b, periodic=True, atwood=0.5, g=1.0, fp32c=True)
+        zm.zm_set_far_path(alone.h, zm.ZM_FAR_TENSOR)
+        ua = alone.velocity(*states[k], want_wdot=False)
+        alone.close()
+        assert np.array_equal(ub, ua), k
+    zm.zm_batch_destroy(h)

@@ -41,6 +41,38 @@ __global__ void __launch_bounds__(kTpb)
     if (write_phi) phi[p] = q[p] + 0.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
 }
 
+// The same reduction for many splits and few points (small meshes, where the all-pairs pass
+// splits the sources into dozens of slices to fill the GPU): kG threads per point each sum the
+// splits g, g + kG, ..., and the kG partial sums are added in a fixed order through shared
+// memory, so the result is deterministic (though associated differently from reduce_kernel).
+constexpr int kRedG = 8;
+__global__ void __launch_bounds__(kTpb)
+    reduce_wide_kernel(int N, int nsplit, const double *__restrict__ part, const double *__restrict__ q,
+                       double *__restrict__ u, double *__restrict__ phi, int write_phi)
+{
+    __shared__ double sh[3][kRedG][kTpb / kRedG];
+    const int lp = threadIdx.x % (kTpb / kRedG), g = threadIdx.x / (kTpb / kRedG);
+    const int p = blockIdx.x * (kTpb / kRedG) + lp;
+    double s[3] = {0.0, 0.0, 0.0};
+    if (p < N)
+        for (int k = g; k < nsplit; k += kRedG) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s[c] += part[((size_t)k * 3 + c) * N + p];
+        }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sh[c][g][lp] = s[c];
+    __syncthreads();
+    if (g != 0 || p >= N) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double t = sh[c][0][lp];
+        for (int h = 1; h < kRedG; ++h) t += sh[c][h][lp];
+        s[c] = t;
+        u[(size_t)c * N + p] = t;
+    }
+    if (write_phi) phi[p] = q[p] + 0.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+}
+
 template <bool kVisc, int kMode>
 __global__ void __launch_bounds__(kTpb)
     vorticity_kernel(Geom g, const double *__restrict__ phi, const double *__restrict__ y,
@@ -106,8 +138,12 @@ int launch_reduce(zm_ctx *c, bool write_phi)
     dim3 grid((g.N + kTpb - 1) / kTpb);
     cudaEvent_t ev = nullptr;
     prof_begin(c, ZM_K_REDUCE, &ev);
-    reduce_kernel<<<grid, kTpb, 0, c->stream>>>(g.N, c->plan.nsplit, c->part, c->q, c->u, c->phi,
-                                                write_phi ? 1 : 0);
+    if (c->plan.nsplit >= 4 * kRedG && g.N <= 16 * kTpb * 152)
+        reduce_wide_kernel<<<(g.N + kTpb / kRedG - 1) / (kTpb / kRedG), kTpb, 0, c->stream>>>(
+            g.N, c->plan.nsplit, c->part, c->q, c->u, c->phi, write_phi ? 1 : 0);
+    else
+        reduce_kernel<<<grid, kTpb, 0, c->stream>>>(g.N, c->plan.nsplit, c->part, c->q, c->u, c->phi,
+                                                    write_phi ? 1 : 0);
     prof_end(c, ZM_K_REDUCE, ev);
     return cuda_check(cudaGetLastError(), "reduce kernel launch");
 }

@@ -66,7 +66,7 @@ def parse():
                     help="also serve both traces with the all-resident first-come-first-served policy")
     ap.add_argument("--case", nargs=3, metavar=("KIND", "SIZE", "STEPS"),
                     help="run one small fixed workload for a profiler and exit (no timing, no JSON): "
-                         "KIND is low | lowdf | high32 | high64 | batch | single")
+                         "KIND is low | lowdf | high32 | high32tc | high64 | batch | single")
     return ap.parse_args()
 
 
@@ -327,6 +327,7 @@ def run_case(kind, size, steps):
       low SIZE STEPS      low order, FP64, SIZE^2 periodic 8-mode interface with vorticity
       lowdf SIZE STEPS    the same in double words
       high32 SIZE STEPS   high order, FP32C pair terms
+      high32tc SIZE STEPS the same with the far tile pairs on the tensor cores (opt-in path)
       high64 SIZE STEPS   high order, FP64
       batch COUNT STEPS   COUNT ragged interfaces (sides 64-384), FP32C batch
       single SIZE STEPS   single mode on free edges, FP64"""
@@ -352,14 +353,16 @@ def run_case(kind, size, steps):
         model.sync()
         model.close()
         return 0
-    if kind not in ("low", "lowdf", "high32", "high64"):
+    if kind not in ("low", "lowdf", "high32", "high32tc", "high64"):
         print(run_case.__doc__)
         return 2
     order = zm.ZM_ORDER_LOW if kind in ("low", "lowdf") else zm.ZM_ORDER_HIGH
     z, _ = inputs.multi_mode(size, n_modes=8, seed=7, amp=0.02)
     _, w = inputs.random_state(size, seed=3)
-    model = zm.ZModel(size, periodic=True, atwood=0.7, g=1.0, order=order, fp32c=(kind == "high32"),
-                      df64=(kind == "lowdf"))
+    model = zm.ZModel(size, periodic=True, atwood=0.7, g=1.0, order=order,
+                      fp32c=kind in ("high32", "high32tc"), df64=(kind == "lowdf"))
+    if kind == "high32tc":
+        zm.zm_set_far_path(model.h, zm.ZM_FAR_TENSOR)
     model.set_state(z, w)
     model.step(1e-3, steps)
     model.sync()

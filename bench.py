@@ -859,8 +859,8 @@ def run_gb300(args):
         if not args.no_serve:
             extras["serving"] = bench_serving(zm, inputs, compare=args.serve_compare)
 
-    # the same 256^2 all-pairs sum with its far tile pairs on the CUDA cores instead of the
-    # tensor cores (same work items; the headline uses the tensor-core far path)
+    # the same 256^2 all-pairs sum with its far tile pairs on the tensor cores beside the
+    # CUDA cores (same work items; the headline uses the CUDA-core far path)
     if not args.no_extras:
         mc = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=0.1 / n, fp32c=True,
                        stream=torch.cuda.current_stream().cuda_stream)

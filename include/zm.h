@@ -260,10 +260,10 @@ int zm_batch_set_tile_shape(zm_batch *b, int32_t tp1, int32_t tp2);
  *   ZM_FAR_TENSOR          K on the CUDA cores, the two sums as one matrix product K [g | m]
  *                          on the tensor cores (TF32 operands split into a TF32 part and a
  *                          TF32 rest, FP32 accumulation in tensor memory over two 8-source
- *                          blocks at a time).  Correct within the FP32C bound but about 3x
- *                          slower on GB300: the 6-column product gives MMAs of N = 16, whose
- *                          issue cost (about 100 cycles each) exceeds the CUDA-core work they
- *                          replace.
+ *                          blocks at a time).  Correct within the FP32C bound but about 1.7x
+ *                          slower on GB300: the 6-column product gives MMAs of N = 16, and
+ *                          handing K to them and waiting for them costs more than the
+ *                          CUDA-core work they replace.
  * Results change within the FP32C bound, not bit for bit.  Rebuilds the plan; synchronous.
  * ZM_ERR_INVALID for another value. */
 #define ZM_FAR_TENSOR 0

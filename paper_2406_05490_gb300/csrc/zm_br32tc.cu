@@ -20,12 +20,14 @@
 // 6.7e-8 against 6.4e-8 relative L2 for the CUDA-core far path).  Near pairs (spheres closer
 // than 1.25 x the radii) stay on the CUDA cores with FP32 hi/lo differences.
 //
-// Measured on GB300 (256^2, one launch): 6.3-7.4 ms against 1.89-1.93 ms for the CUDA-core far path of
-// zm_br32.cu, so it is not the default (ZM_FAR_TENSOR selects it).  Section timers put the cost
-// in the MMA issue: the 6-column product gives MMAs of M = 128, N = 16, K = 8, four per 8-source
-// block (two row groups x Kh, Kl), and issuing them with their commit took ~416 cycles per block
-// against ~262 for the CUDA-core work of the block; deeper A pipelines (2 to 6 slots) and
-// non-suspending waits did not help.
+// Measured on GB300 (256^2, one launch, three CTAs per SM): 3.22 ms against 1.89 ms for the
+// CUDA-core far path of zm_br32.cu, so it is not the default (ZM_FAR_TENSOR selects it).  The
+// hand-offs bound it, not arithmetic: without the MMAs it takes 3.00 ms, without the K
+// arithmetic 2.48 ms.  The 6-column product gives MMAs of M = 128, N = 16, K = 8, four per
+// 8-source block (two row groups x Kh, Kl); one thread issues a tcgen05.mma every ~46 cycles
+// whatever N, so a block costs ~184 cycles of issue against ~128 cycles of MUFU work for its K
+// values, and with two A slots (128 tensor-memory columns per CTA) the compute warps wait on MMA
+// completion.  Polling waits and deeper A pipelines did not help.
 //
 // CTA: 6 warps.  Warps 0-3 compute (thread t owns targets t and t + 128 of the target tile, TMEM
 // lanes t in two 128-row groups); warp 4 lane 0 produces work units (work items from a global
@@ -79,9 +81,8 @@ constexpr uint32_t kLbo = ZM_TC_LBO_IS_K ? kTcStrideK : kTcStrideN;
 constexpr uint32_t kSbo = ZM_TC_LBO_IS_K ? kTcStrideN : kTcStrideK;
 constexpr uint32_t kIdesc = tc::idesc_tf32(128, 16);
 
-// Bounded wait on a phase; false (and the status word set) if it gave up.  (Polling without
-// suspending the thread, mbarrier.test_wait in a loop, measured slower: 7.4 against 6.3 ms per
-// 256^2 launch.)
+// Bounded wait on a phase; false (and the status word set) if it gave up.  (Polling first,
+// mbarrier.test_wait in a loop, or a 64 ns suspend hint measured no faster.)
 __device__ __forceinline__ bool wait_or_flag(uint64_t *bar, uint32_t parity, int *err)
 {
     if (dev::mbar_wait_bounded(bar, parity)) return true;
@@ -458,15 +459,32 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
 
 int br32tc_occupancy()
 {
-    int occ = 0, occ_cut = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, br32tc_kernel<false>, kThreads, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cut, br32tc_kernel<true>, kThreads, 0) != cudaSuccess ||
-        occ < 1 || occ_cut < 1) {
+    // Resident CTAs per SM from the kernel's own resource use.  The runtime's occupancy query
+    // answers one CTA per SM for this kernel (on GB300, also with the largest shared-memory
+    // carveout), while its registers, shared memory and tensor memory leave room for three; run
+    // with three per SM it takes 3.2 instead of 7.4 ms per 256^2 launch.
+    int dev = 0, regs_sm = 0, smem_sm = 0, reserved = 0, threads_sm = 0, blocks_sm = 0;
+    cudaFuncAttributes fa[2];
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&blocks_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa[0], br32tc_kernel<false>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa[1], br32tc_kernel<true>) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
+    int occ = std::min(blocks_sm, threads_sm / kThreads);
+    for (const cudaFuncAttributes &a : fa) {
+        // registers are granted per warp in units of 256
+        const int regs_warp = (a.numRegs * 32 + 255) / 256 * 256;
+        occ = std::min(occ, regs_sm / std::max(regs_warp * (kThreads / 32), 1));
+        occ = std::min(occ, smem_sm / std::max((int)a.sharedSizeBytes + reserved, 1));
+    }
     // tensor memory: 512 columns per SM, kTmemCols per CTA
-    return std::min(std::min(occ, occ_cut), (int)(512 / kTmemCols));
+    return std::max(1, std::min(occ, (int)(512 / kTmemCols)));
 }
 
 int launch_br32tc_batch(const Inst *d_insts, int ninst, long long nitems, int ctas, unsigned long long *counter,

@@ -90,6 +90,21 @@ def test_far_path_rejects_bad_values(zm):
     zm.zm_batch_destroy(h)
 
 
+def test_tensor_path_runs_three_ctas_per_sm(zm):
+    """The tensor-core kernel's residency comes from its own resource use (the runtime's occupancy
+    query answers one CTA per SM for it): its registers, shared memory and 128 tensor-memory
+    columns leave room for three CTAs per SM, against one for the query's answer."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    h = zm.zm_batch_create([(256, 256, 1.0, 1.0, True)], [0.5])
+    cuda_ctas = zm.zm_batch_info(h)["ctas"]
+    zm.zm_batch_set_far_path(h, zm.ZM_FAR_TENSOR)
+    tc_ctas = zm.zm_batch_info(h)["ctas"]
+    zm.zm_batch_destroy(h)
+    print(f"persistent CTAs: CUDA-core kernel {cuda_ctas}, tensor-core kernel {tc_ctas} ({sms} SMs)")
+    assert tc_ctas == 3 * sms and cuda_ctas >= sms
+
+
 def test_tensor_path_with_cutoff_and_in_a_batch(zm):
     """The tensor-core far path under a cutoff (its masked near path and tile skipping), against
     the oracle with the boundary-band treatment of test_gpu_cutoff; and inside a ragged batch,

@@ -163,7 +163,10 @@ def fp64_inst_record():
         except Exception:
             continue
         if h.hexdigest()[:16] == e.get("source_sha256_16"):
-            out[k] = (float(e["thread_inst"]), e.get("n_side"))
+            if "by_side" in e:  # counts that depend on the mesh side: {side: count}
+                out[k] = ({int(n): float(v["thread_inst"]) for n, v in e["by_side"].items()}, "by_side")
+            else:
+                out[k] = (float(e["thread_inst"]), None)
     return out
 
 
@@ -431,9 +434,9 @@ def bench_low_order(zm, torch, inputs, flush, nl, steps, warmup, df64, fp64_tflo
         gbs = b * pts / (t * 1e-3) / 1e9 if t > 0 else 0.0
         kern[k] = {"ms_per_eval": t, "alg_bytes_per_point": b, "alg_gbs": gbs, "hbm_frac": gbs / HBM_GBS}
         if not df64 and fp64_tflops:
-            inst, side = fp64_inst_record().get(k, (None, None))
-            if side is not None and side != nl:
-                inst = None  # counted on another mesh size (per-point count depends on the side)
+            inst, kind = fp64_inst_record().get(k, (None, None))
+            if kind == "by_side":
+                inst = inst.get(nl)  # counted per mesh side; None for a side not counted
             kern[k]["fp64_inst_per_point"] = inst
             kern[k]["fp64_pipe_frac"] = (inst * pts / (t * 1e-3) / (fp64_tflops * 1e12 / 2)
                                          if inst and t > 0 else None)

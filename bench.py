@@ -170,6 +170,24 @@ def fp64_inst_record():
     return out
 
 
+def df64_issue_record():
+    """Warp instructions per point of the double-word low-order kernels by mesh side, counted by
+    ncu on the current kernel sources (profiles/df64_issue_instructions.json); {} if the sources
+    changed since the count (the issue fractions are then reported as null)."""
+    p = os.path.join(ROOT, "profiles", "df64_issue_instructions.json")
+    try:
+        d = json.load(open(p))
+        h = hashlib.sha256()
+        for f in d["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest()[:16] != d.get("source_sha256_16"):
+            return {}
+        return {k: {int(n): float(v["warp_inst"]) for n, v in e["by_side"].items()}
+                for k, e in d["entries"].items()}
+    except Exception:
+        return {}
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -414,7 +432,7 @@ LOW_BYTES = {"geometry": 72, "fft": 144, "vorticity": 152}
 LOW_LAUNCHES_PER_EVAL = {"geometry": 1, "fft": 3, "vorticity": 1}
 
 
-def bench_low_order(zm, torch, inputs, flush, nl, steps, warmup, df64, fp64_tflops=None):
+def bench_low_order(zm, torch, inputs, flush, nl, steps, warmup, df64, fp64_tflops=None, issue_rate=None):
     """Low-order steps on an nl^2 periodic 8-mode interface (amplitude 0.02, A = 0.7): device
     time per step, and per kernel class its time per evaluation and algorithmic HBM GB/s as a
     fraction of the measured copy bandwidth; for the FP64 path also the fraction of the FP64
@@ -433,6 +451,10 @@ def bench_low_order(zm, torch, inputs, flush, nl, steps, warmup, df64, fp64_tflo
         t = profl["ms"][k] / evals
         gbs = b * pts / (t * 1e-3) / 1e9 if t > 0 else 0.0
         kern[k] = {"ms_per_eval": t, "alg_bytes_per_point": b, "alg_gbs": gbs, "hbm_frac": gbs / HBM_GBS}
+        if df64 and issue_rate:
+            inst = df64_issue_record().get(k, {}).get(nl)
+            kern[k]["warp_inst_per_point"] = inst
+            kern[k]["issue_frac"] = inst * pts / (t * 1e-3) / issue_rate if inst and t > 0 else None
         if not df64 and fp64_tflops:
             inst, kind = fp64_inst_record().get(k, (None, None))
             if kind == "by_side":
@@ -445,6 +467,8 @@ def bench_low_order(zm, torch, inputs, flush, nl, steps, warmup, df64, fp64_tflo
             "steps": steps, "steps_per_s": steps / (msl * 1e-3), "ms_per_step": msl / steps,
             "step_alg_gbs": step_bytes / (msl / steps * 1e-3) / 1e9,
             "step_hbm_frac": step_bytes / (msl / steps * 1e-3) / 1e9 / HBM_GBS,
+            "issue_basis": ("ncu-counted warp instructions per point (profiles/df64_issue_instructions.json)"
+                            " x points / time / (SMs x 4 schedulers x sampled SM clock)") if df64 and issue_rate else None,
             "riesz_floor_gbs": 80 * pts / (kern["fft"]["ms_per_eval"] * 1e-3) / 1e9
             if kern["fft"]["ms_per_eval"] > 0 else 0.0,
             "kernels": kern, "hbm_peak_gbs": HBM_GBS, "hbm_peak_basis": "measured copy bandwidth",
@@ -806,8 +830,9 @@ def run_gb300(args):
         extras["fp32c_speedup_vs_fp64"] = value / ws / extras["fp64_plain"]["gpairs_per_s"]
         # low order (FFT Riesz velocity): 1024^2 (the low-vs-high configuration), FP64 and
         # double-word; 4096^2, the largest power-of-two side below the paper's 4864^2 mesh
+        issue_rate = sm_count * 4 * clk_mhz * 1e6  # warp instructions per second at one per scheduler per clock
         extras["low_order_1024"] = bench_low_order(zm, torch, inputs, flush, 1024, 10, 3, False, fp64_peak)
-        extras["low_order_1024_df64"] = bench_low_order(zm, torch, inputs, flush, 1024, 10, 3, True)
+        extras["low_order_1024_df64"] = bench_low_order(zm, torch, inputs, flush, 1024, 10, 3, True, issue_rate=issue_rate)
         # the high-order half of the low-vs-high configuration: the same 8-mode interface
         # (amplitude 0.02, A = 0.7) at 512^2, FP32C all-pairs sum, 10 RK3 steps
         nh = 512
@@ -828,10 +853,10 @@ def run_gb300(args):
             "peak_basis": "measured FP32 FMA probe (as the headline roofline)",
             "kernel_ms_per_step": {k: v / kh for k, v in profh["ms"].items()}}
         extras["low_order_4096"] = bench_low_order(zm, torch, inputs, flush, 4096, 3, 1, False, fp64_peak)
-        extras["low_order_4096_df64"] = bench_low_order(zm, torch, inputs, flush, 4096, 5, 2, True)
+        extras["low_order_4096_df64"] = bench_low_order(zm, torch, inputs, flush, 4096, 5, 2, True, issue_rate=issue_rate)
         # the paper's single-GPU low-order mesh: 4864^2 = (19 x 256)^2, FP64 (radix-19 stage)
         extras["low_order_4864"] = bench_low_order(zm, torch, inputs, flush, 4864, 3, 1, False, fp64_peak)
-        extras["low_order_4864_df64"] = bench_low_order(zm, torch, inputs, flush, 4864, 5, 2, True)
+        extras["low_order_4864_df64"] = bench_low_order(zm, torch, inputs, flush, 4864, 5, 2, True, issue_rate=issue_rate)
         # 32^2 single-mode FP64 (launch bound)
         zs, wsn = inputs.single_mode(32)
         ms_ = zm.ZModel(32, periodic=False, atwood=0.5, g=1.0, delta=0.1 / 32)

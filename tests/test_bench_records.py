@@ -28,3 +28,12 @@ def test_traffic_record_matches_the_headline_kernel():
     t = bench.recorded_traffic((16, 16))
     assert t is not None and t > 0
     assert bench.recorded_traffic((8, 32)) is None  # another tile shape was not captured
+
+
+def test_double_word_instruction_record_matches_the_sources():
+    rec = bench.df64_issue_record()
+    assert set(rec) == {"geometry", "fft", "vorticity"}
+    for k, by_side in rec.items():
+        assert set(by_side) == {1024, 4096, 4864} and all(v > 0 for v in by_side.values())
+    # the transforms grow with log2 of the side and the radix-19 stage of 4864 = 19 x 256
+    assert rec["fft"][1024] < rec["fft"][4096] < rec["fft"][4864]

@@ -2,7 +2,7 @@
 
 * 256^2 multi-mode interface, high order, 20 SSP-RK3 steps: FP32C in the benchmark's launch
   configuration (tile shape and work-item size autotuned on the same interface first, exactly as
-  bench.py does) and FP64.  Reference: the oracle's final state, stored by
+  bench.py does), the same with the far tile pairs on the tensor cores, and FP64.  Reference: the oracle's final state, stored by
   tests/golden/make_stepped.py (which calls only the oracle).
 * 512^2 8-mode interface (amplitude 0.02, A = 0.7), high order, FP32C, one step, autotuned as in
   the benchmark; reference stored the same way.
@@ -56,10 +56,12 @@ def load_golden(name):
     return meta, z0, w0, d["z"], d["w"]
 
 
-def step_on_gpu(zm, meta, z0, w0, fp32c, autotune):
+def step_on_gpu(zm, meta, z0, w0, fp32c, autotune, far_path=None):
     n = meta["n"]
     model = zm.ZModel(n, periodic=True, atwood=meta["atwood"], g=meta["g"], mu=meta["mu"],
                       delta=meta["delta"], fp32c=fp32c)
+    if far_path is not None:
+        zm.zm_set_far_path(model.h, far_path)
     if autotune:
         # as the benchmark: tune on the interface with vorticity, then reset it
         model.set_state(z0, inputs.random_state(n, seed=1)[1])
@@ -83,6 +85,13 @@ def test_multimode_256_twenty_steps(zm, fp32c):
     meta, z0, w0, zr, wr = load_golden("multimode256_20")
     z, w = step_on_gpu(zm, meta, z0, w0, fp32c, autotune=fp32c)
     compare(f"256^2 x 20 steps fp32c={fp32c}", z, w, z0, zr, wr, TOL32 if fp32c else TOL64, meta["steps"])
+
+
+def test_multimode_256_twenty_steps_tensor_far_path(zm):
+    """The same 20 steps with the far tile pairs summed on the tensor cores (opt-in path)."""
+    meta, z0, w0, zr, wr = load_golden("multimode256_20")
+    z, w = step_on_gpu(zm, meta, z0, w0, True, autotune=True, far_path=zm.ZM_FAR_TENSOR)
+    compare("256^2 x 20 steps fp32c, tensor-core far path", z, w, z0, zr, wr, TOL32, meta["steps"])
 
 
 def test_multimode_512_one_step_fp32c(zm):

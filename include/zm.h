@@ -257,13 +257,13 @@ int zm_batch_set_tile_shape(zm_batch *b, int32_t tp1, int32_t tp2);
  * Both evaluate the pair terms in tile-local coordinates, sum_j K_ij (s_j x g_j) - t_i x
  * sum_j K_ij g_j with K_ij = (|s_j - t_i|^2 + delta^2)^(-3/2):
  *   ZM_FAR_CUDA (default)  everything on the CUDA cores (packed FP32x2 instructions);
- *   ZM_FAR_TENSOR          K on the CUDA cores, the two sums as one matrix product K [g | m]
- *                          on the tensor cores (TF32 operands split into a TF32 part and a
- *                          TF32 rest, FP32 accumulation in tensor memory over two 8-source
- *                          blocks at a time).  Correct within the FP32C bound but about 1.7x
- *                          slower on GB300: the 6-column product gives MMAs of N = 16, and
- *                          handing K to them and waiting for them costs more than the
- *                          CUDA-core work they replace.
+ *   ZM_FAR_TENSOR          |s_j - t_i|^2 + delta^2 = |t_i|^2 + Y_ij with the Gram part Y (targets
+ *                          x 4 times 4 x sources) on the tensor cores (TF32 operands split into
+ *                          a TF32 part and a TF32 rest, two MMAs per 128 targets x 32 sources),
+ *                          the rest on the CUDA cores.  Correct within the FP32C bound (the
+ *                          same error as ZM_FAR_CUDA) but about 1.15x slower on GB300: the
+ *                          hand-off and packing work it adds outweighs the arithmetic it
+ *                          removes.
  * Results change within the FP32C bound, not bit for bit.  Rebuilds the plan; synchronous.
  * ZM_ERR_INVALID for another value. */
 #define ZM_FAR_TENSOR 0

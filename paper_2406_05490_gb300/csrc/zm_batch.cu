@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kPtb)
     if (p >= I.geom.N || !ZM_IDX_OK(p, I.geom.N)) return;
     const double pref = I.geom.dx1 * I.geom.dx2 / (4.0 * 3.14159265358979323846);
     geometry_point<kGeoFp32c>(I.geom, I.tiling, p, I.y[yin], pref, I.g, (float)(I.delta * I.delta),
-                              I.near_rec, I.far_rec, I.tinfo, I.gmax, I.q, nullptr, I.tc_rec != 0);
+                              I.near_rec, I.far_rec, I.tinfo, I.gmax, I.q, nullptr);
 }
 
 // u = fixed-point sum * 2^-scale, Phi = q + |u|^2 / 2; clears the accumulators, the tile
@@ -229,7 +229,6 @@ int Batch::plan()
     long long items = 0;
     int blocks = 0;
     for (auto &I : h) {
-        I.tc_rec = tc ? 1 : 0;
         I.block0 = blocks;
         blocks += (I.geom.N + kPtb - 1) / kPtb;
         I.chunk = chunk_override > 0 ? std::min(chunk_override, I.tiling.ntiles)

@@ -1,44 +1,39 @@
 // zm_br32tc.cu -- FP32-compensated all-pairs Birkhoff-Rott sum over a batch of interfaces with
-// the far-field accumulation on the tensor cores (paper Sec. 2 BRSolver, Sec. 3.2.1
+// the far pairs' |z_j - z_i|^2 formed on the tensor cores (paper Sec. 2 BRSolver, Sec. 3.2.1
 // ExactBRSolver, the high-order model):
 //     u_i = sum_j (z_j - z_i) x gamma'_j / (|z_j - z_i|^2 + delta^2)^(3/2),   i, j in one interface.
 //
-// Work units, near/far classification, cutoff handling and fixed-point accumulation are those of
-// zm_br32.cu (same work items, same tile spheres, same 64-bit fixed point); what differs is how
-// a far (target tile, source tile) pair is summed.  In tile-local coordinates (s_j = z_j - c_S,
-// t_i = z_i - c_S) a far pair contributes K_ij (s_j x g_j) - t_i x K_ij g_j with
-// K_ij = (|s_j - t_i|^2 + delta^2)^(-3/2), so the tile's contribution to target i is
-//     v_i = sum_j K_ij m_j - t_i x sum_j K_ij g_j,   m_j = s_j x g_j,
-// and the two sums are one matrix product: the 256 x 256 matrix K times the tile's 256 x 6 source
-// matrix [g | m].  The CUDA cores form K (|s - t|^2 + delta^2 in Gram form, one MUFU rsqrt, its
-// cube: 6 FP32 lane operations per pair, packed two per instruction); the tensor cores do the
-// product (tcgen05.mma kind::tf32, accumulating in FP32 in tensor memory).  Each operand is split
-// into a TF32 part and a TF32 rest (K = Kh + Kl, B = Bh + Bl), and with B's columns laid out as
-// [Bh | Bl] (16 columns) two MMAs per 8 sources, Kh [Bh | Bl] + Kl [Bh | Bl], give all four
-// partial products; their column pairs are added when tensor memory is read.  That keeps about
-// 21 significant bits per product, the accuracy of the FP32 path (a float32 emulation at 256^2:
-// 6.7e-8 against 6.4e-8 relative L2 for the CUDA-core far path).  Near pairs (spheres closer
-// than 1.25 x the radii) stay on the CUDA cores with FP32 hi/lo differences.
+// Work units, near/far classification, cutoff handling, records and fixed-point accumulation are
+// those of zm_br32.cu; what differs is how a far (target tile, source tile) pair forms its
+// kernel values.  In tile-local coordinates (t_i = z_i - c_S, s_j = z_j - c_S, c_S the source
+// tile's centre)
+//     q_ij = |t_i|^2 + Y_ij,   Y_ij = (|s_j|^2 + delta^2) - 2 t_i . s_j,
+// and Y is a matrix product: A (row i: -2 t_i, 1) times B (column j: s_j, |s_j|^2 + delta^2),
+// K = 4.  Both operands are split into a TF32 part and a TF32 rest; two MMAs (kind::tf32, K = 8,
+// M = 128 targets, N = 32 sources) give (A_hi + A_lo)(B_hi + B_lo): the first reads
+// [A_hi | A_hi] against [B_hi ; B_lo], the second [A_lo | A_lo] (the same 4-column core matrix
+// read twice, descriptor stride 0 along K).  |t_i|^2, the term of q's own size, is added on the
+// CUDA cores, so the tensor cores' FP32 accumulation, which truncates toward zero, only touches
+// the smaller Y, over one product of 16 terms (a float32 emulation at 256^2: 7.0e-8 relative L2
+// against 6.9e-8 for the CUDA-core Gram form; measured 1.37e-7 on u for both paths).  The CUDA
+// cores then take the reciprocal square root, its cube and the six accumulations
+// sum_j K (s_j x g_j), sum_j K g_j -- 9 FP32 lane operations per pair instead of 12.
 //
-// Measured on GB300 (256^2, one launch, three CTAs per SM): 3.22 ms against 1.89 ms for the
-// CUDA-core far path of zm_br32.cu, so it is not the default (ZM_FAR_TENSOR selects it).  The
-// hand-offs bound it, not arithmetic: without the MMAs it takes 3.00 ms, without the K
-// arithmetic 2.48 ms.  The 6-column product gives MMAs of M = 128, N = 16, K = 8, four per
-// 8-source block (two row groups x Kh, Kl); one thread issues a tcgen05.mma every ~46 cycles
-// whatever N, so a block costs ~184 cycles of issue against ~128 cycles of MUFU work for its K
-// values, and with two A slots (128 tensor-memory columns per CTA) the compute warps wait on MMA
-// completion.  Polling waits and deeper A pipelines did not help.
+// Measured on GB300 (256^2, one launch): 2.18 ms against 1.89 ms for zm_br32.cu, so it is not the
+// default (ZM_FAR_TENSOR selects it).  ncu: issue 56 %, FMA pipe 54 %, 10.4 thread instructions
+// per pair; the warps wait on fixed-latency dependencies and tensor-memory loads with three
+// compute warps per scheduler.  Sweeps (chunks of 16 / 32 / 64 sources, one or two operand
+// buffers, 2-4 CTAs per SM, one load of a whole chunk, scalar K) did not beat this layout.
 //
-// CTA: 6 warps.  Warps 0-3 compute (thread t owns targets t and t + 128 of the target tile, TMEM
-// lanes t in two 128-row groups); warp 4 lane 0 produces work units (work items from a global
-// atomic counter, tile records by 1D bulk TMA into a double-buffered stage); warp 5 lane 0 issues
-// the MMAs.  Hand-offs are mbarriers: record full / free per stage, A slot full / empty per
-// 8-source block (K values in tensor memory), D full / empty per accumulation segment (two
-// accumulator buffers; the compute warps add segment q after submitting segment q + 1).  Every wait is bounded: a wait that gives up sets the status word, and the role
-// leaves its loop; the others then give up in turn.
-//
-// Tensor memory (128 columns per CTA): D, two buffers x two row groups x 16 columns (columns
-// 0-63); A, two slots x two row groups x (8 columns Kh + 8 columns Kl) (columns 64-127).
+// CTA: 6 warps.  Warps 0-3 compute (thread t owns targets t and t + 128 of the target tile, i.e.
+// tensor-memory lane t in two row groups); warp 4 takes work items from a global atomic counter,
+// copies the source records by 1D bulk TMA into a double-buffered stage and, for a far unit,
+// writes the unit's operands A (256 targets) and B (256 sources) into shared memory (two
+// buffers); warp 5 lane 0 issues the MMAs.  Hand-offs are mbarriers: record full / free per
+// stage, operands full / empty per buffer, accumulator full / empty per row group and buffer
+// (two 32-column accumulators per row group in tensor memory).  Every wait is bounded: a wait
+// that gives up sets the status word and the role leaves its loop; the others then give up in
+// turn.  Tensor memory: 128 columns per CTA.
 #include <algorithm>
 
 #include "zm_br32_common.cuh"
@@ -47,42 +42,26 @@
 namespace zm {
 namespace {
 
-constexpr int kCW = 4;            // compute warps
-constexpr int kCT = kCW * 32;     // compute threads: 128 rows per group
-constexpr int kThreads = kCT + 64;  // + producer warp + MMA warp
-#ifndef ZM_BR32TC_NA
-#define ZM_BR32TC_NA 2
-#endif
-constexpr int kNA = ZM_BR32TC_NA;  // A slots (8-source blocks in flight)
-constexpr int kBlocks = kTs / 8;  // 8-source blocks per source tile
-// Accumulation segments: the MMAs accumulate in tensor memory over kSeg blocks only, then start
-// a fresh accumulator; the compute warps add the segments in FP32 registers (round to nearest).
-// The tensor cores' FP32 accumulation truncates toward zero, so its error grows with the length
-// of an accumulation chain and does not average out (a 64-MMA chain per tile gave 1.6e-6
-// relative L2 at 256^2).
-#ifndef ZM_BR32TC_SEG
-#define ZM_BR32TC_SEG 2
-#endif
-constexpr int kSeg = ZM_BR32TC_SEG;
-static_assert(kBlocks % kSeg == 0, "segments must tile the source blocks");
-constexpr uint32_t kColD = 0, kColA = 64;
-constexpr uint32_t kTmemNeed = kColA + 32 * kNA;
-constexpr uint32_t kTmemCols = kTmemNeed <= 128 ? 128 : kTmemNeed <= 256 ? 256 : 512;
-constexpr int kStageRows = 20;    // far: s, |s|^2 + delta^2, B (rows 0-19 of the record); near: 9 rows
+constexpr int kCW = 4;               // compute warps
+constexpr int kCT = kCW * 32;        // compute threads: 128 rows per row group
+constexpr int kThreads = kCT + 64;   // + producer warp + MMA warp
+constexpr int kChunk = 32;           // sources per accumulator (the MMA's N)
+constexpr int kNChunks = kTs / kChunk;
+constexpr int kAB = 2;               // operand buffers
+constexpr uint32_t kTmemCols = 4 * kChunk;  // two row groups x two accumulator buffers
+__host__ __device__ constexpr uint32_t col_d(int g, int b) { return (uint32_t)(kChunk * (2 * b + g)); }
+constexpr int kStageRows = 10;       // far: s (3), |s|^2 + delta^2, strength (3), s x strength (3)
 constexpr float kFarFactor = 1.25f;
-#ifndef ZM_BR32TC_MINB
-#define ZM_BR32TC_MINB (ZM_BR32TC_NA <= 2 ? 3 : 2)
-#endif
-// K-major, no swizzle: which descriptor field holds the K-direction stride
-#ifndef ZM_TC_LBO_IS_K
-#define ZM_TC_LBO_IS_K 1
-#endif
-constexpr uint32_t kLbo = ZM_TC_LBO_IS_K ? kTcStrideK : kTcStrideN;
-constexpr uint32_t kSbo = ZM_TC_LBO_IS_K ? kTcStrideN : kTcStrideK;
-constexpr uint32_t kIdesc = tc::idesc_tf32(128, 16);
+constexpr uint32_t kIdesc = tc::idesc_tf32(128, kChunk);
+// Operand layout, K-major without swizzling (core matrices of 8 rows x 16 bytes): row r (a target
+// of A, a source of B), part h (0: TF32 part, 1: rest), k < 4 at float op_off(r, h, k), i.e. byte
+// (r / 8) 256 + h 128 + (r % 8) 16 + 4 k: the descriptors' stride along K is 128 bytes for B (part
+// 0 then part 1) and 0 for A (one part read twice), along M / N 256 bytes.
+constexpr int kOpFloatsA = 128 * 8;  // per row group
+constexpr int kOpFloatsB = kTs * 8;
+__device__ __forceinline__ int op_off(int r, int h, int k) { return (r >> 3) * 64 + h * 32 + (r & 7) * 4 + k; }
 
-// Bounded wait on a phase; false (and the status word set) if it gave up.  (Polling first,
-// mbarrier.test_wait in a loop, or a 64 ns suspend hint measured no faster.)
+// Bounded wait on a phase; false (and the status word set) if it gave up.
 __device__ __forceinline__ bool wait_or_flag(uint64_t *bar, uint32_t parity, int *err)
 {
     if (dev::mbar_wait_bounded(bar, parity)) return true;
@@ -91,7 +70,7 @@ __device__ __forceinline__ bool wait_or_flag(uint64_t *bar, uint32_t parity, int
 }
 
 // The same for a whole warp: lane 0 waits, and the warp goes on only if it saw the phase
-// complete (so that the warp-collective tensor-memory moves after it stay converged).
+// complete (so that the warp-collective tensor-memory loads after it stay converged).
 __device__ __forceinline__ bool warp_wait_or_flag(uint64_t *bar, uint32_t parity, int *err)
 {
     bool ok = true;
@@ -108,18 +87,34 @@ struct Unit {
     int path;  // 0 near, 1 far, 2 near masked at the cutoff
 };
 
+// v = hi + lo with hi the TF32 value nearest v and lo the TF32 value nearest the rest
+__device__ __forceinline__ void split4(const float v[4], float hi[4], float lo[4])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        hi[k] = dev::tf32_round(v[k]);
+        lo[k] = dev::tf32_round(v[k] - hi[k]);
+    }
+}
+
+__device__ __forceinline__ void st_part(float *base, int r, int h, const float v[4])
+{
+    *reinterpret_cast<float4 *>(base + op_off(r, h, 0)) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
 template <bool kCut>
-__global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
+__global__ void __launch_bounds__(kThreads, 3)
     br32tc_kernel(const Inst *__restrict__ insts, int ninst, long long nitems, unsigned long long *counter,
                   int *err)
 {
     __shared__ __align__(1024) float stage[2][kStageRows * kTs];
+    __shared__ __align__(1024) float opA[kAB][2][kOpFloatsA];  // [buffer][row group]
+    __shared__ __align__(1024) float opB[kAB][kOpFloatsB];
     __shared__ long long acc[3][2][kCT];
-    __shared__ __align__(8) uint64_t rec_full[2], rec_free[2], a_full[kNA], a_empty[kNA], d_full[2], d_empty[2];
-    __shared__ __align__(8) uint64_t mma_drain;
+    __shared__ __align__(8) uint64_t rec_full[2], rec_free[2], ab_full[kAB], ab_empty[kAB];
+    __shared__ __align__(8) uint64_t d_full[2][2], d_empty[2][2], mma_drain;
     __shared__ Unit unit[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -127,16 +122,17 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
         for (int k = 0; k < 2; ++k) {
             dev::mbar_init(&rec_full[k], 1);
             dev::mbar_init(&rec_free[k], kCW + 1);
-            dev::mbar_init(&d_full[k], 1);
-            dev::mbar_init(&d_empty[k], kCW);
-        }
-        for (int k = 0; k < kNA; ++k) {
-            dev::mbar_init(&a_full[k], kCW);
-            dev::mbar_init(&a_empty[k], 1);
+            if (k < kAB) {
+                dev::mbar_init(&ab_full[k], 1);
+                dev::mbar_init(&ab_empty[k], 1);
+            }
+            for (int g = 0; g < 2; ++g) {
+                dev::mbar_init(&d_full[g][k], 1);
+                dev::mbar_init(&d_empty[g][k], kCW);
+            }
         }
         dev::mbar_init(&mma_drain, 1);
         dev::fence_mbar_init();
-        abort_flag = 0;
     }
     if (warp == 0) {
         tc::alloc(&tmem_base, kTmemCols);
@@ -152,17 +148,18 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
     const uint32_t tbase = tmem_base;
 
     if (warp == kCW) {
-        // ---------------- producer: work units and their records ----------------
-        if (lane == 0) {
-            int p_inst = 0, p_tile = 0, p_next = 0, p_left = 0;
-            bool done = false, clean = false;
-            int last_copy[2] = {-1, -1};  // unit whose record was last copied into each stage
-            for (int u = 0;; ++u) {
-                const int s = u & 1;
-                if (u >= 2 && !wait_or_flag(&rec_free[s], ((u - 2) >> 1) & 1, err)) break;
-                if (*(volatile int *)&abort_flag) break;
-                Unit un;
-                un.inst = -1;
+        // ------------- producer: work units, their records, and the far units' operands -------------
+        int p_inst = 0, p_tile = 0, p_next = 0, p_left = 0;
+        bool done = false, clean = false;
+        int last_copy[2] = {-1, -1};
+        int fcount = 0;
+        for (int u = 0;; ++u) {
+            const int s = u & 1;
+            if (u >= 2 && !warp_wait_or_flag(&rec_free[s], ((u - 2) >> 1) & 1, err)) break;
+            Unit un;
+            un.inst = -1;
+            un.tile = un.src = un.path = 0;
+            if (lane == 0) {
                 while (!done) {
                     while (p_left == 0 && !done) {
                         const long long it = (long long)atomicAdd(counter, 1ull);
@@ -170,7 +167,7 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
                             done = true;
                             break;
                         }
-                        int lo = 0, hi = ninst - 1;  // last interface with item0 <= it
+                        int lo = 0, hi = ninst - 1;
                         while (lo < hi) {
                             const int mid = (lo + hi + 1) >> 1;
                             if (insts[mid].item0 <= it) lo = mid;
@@ -196,8 +193,8 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
                     int path = (D >= kFarFactor * (a.w + b.w)) ? 1 : 0;
                     if (kCut && I.cutoff > 0.0) {
                         const float c = (float)I.cutoff;
-                        if (D - a.w - b.w > c * 1.0001f) continue;   // every pair beyond c
-                        if (D + a.w + b.w >= c * 0.9999f) path = 2;  // straddles c: masked near
+                        if (D - a.w - b.w > c * 1.0001f) continue;
+                        if (D + a.w + b.w >= c * 0.9999f) path = 2;
                     }
                     un.inst = p_inst;
                     un.tile = p_tile;
@@ -209,31 +206,68 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
                 if (un.inst < 0) {
                     dev::mbar_arrive(&rec_full[s]);  // the end marker
                     clean = true;
-                    break;
-                }
-                last_copy[s] = u;
-                const Inst &I = insts[un.inst];
-                if (un.path == 1) {
-                    dev::mbar_expect_tx(&rec_full[s], kStageRows * kTs * sizeof(float));
-                    dev::tma_copy_1d(stage[s], I.far_rec + (size_t)un.src * kRec32F * kTs,
-                                     kStageRows * kTs * sizeof(float), &rec_full[s]);
                 } else {
-                    dev::mbar_expect_tx(&rec_full[s], kRec32 * kTs * sizeof(float));
-                    dev::tma_copy_1d(stage[s], I.near_rec + (size_t)un.src * kRec32 * kTs,
-                                     kRec32 * kTs * sizeof(float), &rec_full[s]);
+                    last_copy[s] = u;
+                    const Inst &I = insts[un.inst];
+                    if (un.path == 1) {
+                        const float *rec = I.far_rec + (size_t)un.src * kRec32F * kTs;
+                        dev::mbar_expect_tx(&rec_full[s], kStageRows * kTs * sizeof(float));
+                        dev::tma_copy_1d(stage[s], rec, 4 * kTs * sizeof(float), &rec_full[s]);
+                        dev::tma_copy_1d(stage[s] + 4 * kTs, rec + kFarRowG * kTs, 6 * kTs * sizeof(float),
+                                         &rec_full[s]);
+                    } else {
+                        dev::mbar_expect_tx(&rec_full[s], kRec32 * kTs * sizeof(float));
+                        dev::tma_copy_1d(stage[s], I.near_rec + (size_t)un.src * kRec32 * kTs,
+                                         kRec32 * kTs * sizeof(float), &rec_full[s]);
+                    }
                 }
             }
-            // after an abnormal exit, let this thread's copies still in flight land before the
-            // CTA's shared memory is released (bounded as well)
-            if (!clean)
-                for (int k = 0; k < 2; ++k)
-                    if (last_copy[k] >= 0 && !dev::mbar_wait_bounded(&rec_full[k], (last_copy[k] >> 1) & 1))
-                        atomicOr(err, kErrDrain);
+            un.inst = __shfl_sync(0xffffffffu, un.inst, 0);
+            un.tile = __shfl_sync(0xffffffffu, un.tile, 0);
+            un.src = __shfl_sync(0xffffffffu, un.src, 0);
+            un.path = __shfl_sync(0xffffffffu, un.path, 0);
+            if (un.inst < 0) break;
+            if (un.path != 1) continue;
+            // far unit: its operands A (targets) and B (sources) into buffer fcount % kAB
+            const int buf = fcount % kAB;
+            if (fcount >= kAB && !warp_wait_or_flag(&ab_empty[buf], ((fcount - kAB) / kAB) & 1, err)) break;
+            if (!warp_wait_or_flag(&rec_full[s], (u >> 1) & 1, err)) break;
+            const Inst &I = insts[un.inst];
+            const float4 cs = I.tinfo[un.src];
+            const float *st = stage[s];
+            const float *tgt = I.near_rec + (size_t)un.tile * kRec32 * kTs;
+            for (int j = lane; j < kTs; j += 32) {
+                // source j: (s, |s|^2 + delta^2)
+                float v[4] = {st[j], st[kTs + j], st[2 * kTs + j], st[3 * kTs + j]}, hi[4], lo[4];
+                split4(v, hi, lo);
+                st_part(opB[buf], j, 0, hi);
+                st_part(opB[buf], j, 1, lo);
+                const float *tr = tgt + j;
+                const float tx = (__ldg(tr) - cs.x) + __ldg(tr + 3 * kTs);
+                const float ty = (__ldg(tr + kTs) - cs.y) + __ldg(tr + 4 * kTs);
+                const float tz = (__ldg(tr + 2 * kTs) - cs.z) + __ldg(tr + 5 * kTs);
+                // target slot j (row j % 128 of row group j / 128): (-2 t, 1), t as the compute
+                // warps form it
+                float a[4] = {-2.0f * tx, -2.0f * ty, -2.0f * tz, 1.0f};
+                split4(a, hi, lo);
+                st_part(opA[buf][j >> 7], j & 127, 0, hi);
+                st_part(opA[buf][j >> 7], j & 127, 1, lo);
+            }
+            dev::fence_proxy_async();  // the tensor cores read what the threads wrote
+            __syncwarp();
+            if (lane == 0) dev::mbar_arrive(&ab_full[buf]);
+            ++fcount;
         }
+        // after an abnormal exit, let this warp's copies in flight land before shared memory is
+        // released (bounded as well)
+        if (lane == 0 && !clean)
+            for (int k = 0; k < 2; ++k)
+                if (last_copy[k] >= 0 && !dev::mbar_wait_bounded(&rec_full[k], (last_copy[k] >> 1) & 1))
+                    atomicOr(err, kErrDrain);
     } else if (warp == kCW + 1) {
-        // ---------------- MMA issuer ----------------
+        // ---------------- MMA issuer: Y = A B per row group and 32-source chunk ----------------
         if (lane == 0) {
-            int f = 0, g = 0;
+            int fcount = 0, dcnt = 0;
             for (int u = 0;; ++u) {
                 const int s = u & 1;
                 if (!wait_or_flag(&rec_full[s], (u >> 1) & 1, err)) break;
@@ -241,39 +275,35 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
                 if (un.inst < 0) break;
                 bool ok = true;
                 if (un.path == 1) {
-                    const char *bmat = reinterpret_cast<const char *>(stage[s] + kFarRowB * kTs);
-                    int db = 0;
-                    for (int kb = 0; kb < kBlocks && ok; ++kb, ++g) {
-                        if (kb % kSeg == 0) {  // a new segment q = f: a fresh accumulator
-                            db = f & 1;
-                            if (f >= 2 && !wait_or_flag(&d_empty[db], ((f - 2) >> 1) & 1, err)) {
-                                ok = false;
-                                break;
+                    const int buf = fcount % kAB;
+                    ok = wait_or_flag(&ab_full[buf], (fcount / kAB) & 1, err);
+                    if (ok) {
+                        tc::fence_after();
+                        const char *pb = reinterpret_cast<const char *>(opB[buf]);
+                        for (int c = 0; c < kNChunks && ok; ++c, ++dcnt) {
+                            const int b = dcnt & 1;
+                            const uint64_t bd = tc::smem_desc(pb + 32 * kChunk * c, 128, 256);
+#pragma unroll
+                            for (int g = 0; g < 2; ++g) {
+                                if (dcnt >= 2 && !wait_or_flag(&d_empty[g][b], ((dcnt - 2) >> 1) & 1, err)) {
+                                    ok = false;
+                                    break;
+                                }
+                                tc::fence_after();
+                                const char *pa = reinterpret_cast<const char *>(opA[buf][g]);
+                                const uint32_t d = tbase + col_d(g, b);
+                                // K-step 0: [A_hi | A_hi] x [B_hi; B_lo]; K-step 1: [A_lo | A_lo] x [B_hi; B_lo]
+                                tc::mma_tf32_ss(d, tc::smem_desc(pa, 0, 256), bd, kIdesc, false);
+                                tc::mma_tf32_ss(d, tc::smem_desc(pa + 128, 0, 256), bd, kIdesc, true);
+                                tc::commit(&d_full[g][b]);
                             }
                         }
-                        const int a = g % kNA;
-                        if (!wait_or_flag(&a_full[a], (g / kNA) & 1, err)) {
-                            ok = false;
-                            break;
-                        }
-                        tc::fence_after();
-                        const uint64_t bd = tc::smem_desc(bmat + kb * 512, kLbo, kSbo);
-#pragma unroll
-                        for (int grp = 0; grp < 2; ++grp) {
-                            const uint32_t d = tbase + kColD + db * 32 + grp * 16;
-                            const uint32_t ah = tbase + kColA + a * 32 + grp * 16;
-                            tc::mma_tf32_ts(d, ah, bd, kIdesc, kb % kSeg != 0);
-                            tc::mma_tf32_ts(d, ah + 8, bd, kIdesc, true);
-                        }
-                        tc::commit(&a_empty[a]);
-                        if (kb % kSeg == kSeg - 1) {
-                            tc::commit(&d_full[db]);
-                            ++f;
-                        }
+                        if (ok) tc::commit(&ab_empty[buf]);
                     }
-                    if (!ok) break;
+                    ++fcount;
                 }
                 dev::mbar_arrive(&rec_free[s]);
+                if (!ok) break;
             }
             // every MMA issued above has completed before tensor memory is released
             tc::commit(&mma_drain);
@@ -284,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
         int c_inst = -1, c_tile = -1;
         float c_d2 = 0.0f, c_mult = 1.0f, c_c2 = 0.0f;
         const float *c_near = nullptr;
-        int f = 0, g = 0;
+        int dcnt = 0;
         bool ok = true;
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
 
@@ -293,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
             const Inst &I = insts[c_inst];
             const int ti = c_tile / I.tiling.nt2, tj = c_tile - ti * I.tiling.nt2;
             const size_t N = I.geom.N;
-            const int lg2 = __ffs(I.tiling.tp2) - 1;  // tp2 is a power of two
+            const int lg2 = __ffs(I.tiling.tp2) - 1;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 const int slot = r * kCT + tid;
@@ -323,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
                 if (un.inst != c_inst) {
                     const Inst &I = insts[un.inst];
                     const int sc = fix_scale(I);
-                    c_mult = __int_as_float((127 + sc) << 23);  // 2^scale, exact
+                    c_mult = __int_as_float((127 + sc) << 23);
                     c_d2 = (float)(I.delta * I.delta);
                     c_c2 = (float)(I.cutoff * I.cutoff);
                     c_near = I.near_rec;
@@ -334,105 +364,72 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
             }
             const float *st = stage[s];
             if (un.path == 1) {
-                // ---- far: K on the CUDA cores, K [g | m] on the tensor cores ----
+                // ---- far: q = |t|^2 + Y, Y from the tensor cores ----
                 const float4 cs = insts[c_inst].tinfo[un.src];
-                u64 m2x[2], m2y[2], m2z[2], bb[2];
                 float tx[2], ty[2], tz[2];
+                u64 bb[2], ax[2], ay[2], az[2], gxs[2], gys[2], gzs[2];
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
                     const float *tr = c_near + (size_t)c_tile * kRec32 * kTs + r * kCT + tid;
                     tx[r] = (__ldg(tr) - cs.x) + __ldg(tr + 3 * kTs);
                     ty[r] = (__ldg(tr + kTs) - cs.y) + __ldg(tr + 4 * kTs);
                     tz[r] = (__ldg(tr + 2 * kTs) - cs.z) + __ldg(tr + 5 * kTs);
-                    m2x[r] = pack2(-2.0f * tx[r], -2.0f * tx[r]);
-                    m2y[r] = pack2(-2.0f * ty[r], -2.0f * ty[r]);
-                    m2z[r] = pack2(-2.0f * tz[r], -2.0f * tz[r]);
                     const float b1 = fmaf(tx[r], tx[r], fmaf(ty[r], ty[r], tz[r] * tz[r]));
                     bb[r] = pack2(b1, b1);
+                    ax[r] = ay[r] = az[r] = gxs[r] = gys[r] = gzs[r] = 0ull;
                 }
                 const u64 *s2 = reinterpret_cast<const u64 *>(st);  // row k: sources (2m, 2m + 1)
-                // running FP32 sums of this unit's segments: sum K g (b) and sum K m (a) per target
-                float sb[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, sm[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-                // add segment q (accumulator buffer q & 1) once its MMAs completed, then free it
-                auto read_segment = [&](int q) -> bool {
-                    const int db = q & 1;
-                    if (!warp_wait_or_flag(&d_full[db], (q >> 1) & 1, err)) return false;
-                    tc::fence_after();
-                    uint32_t dv[2][16];
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) tc::ld16(tbase + lane_base + kColD + db * 32 + r * 16, dv[r]);
-                    tc::wait_ld();
-                    tc::fence_before();
-                    __syncwarp();
-                    if (lane == 0) dev::mbar_arrive(&d_empty[db]);
-#pragma unroll
-                    for (int r = 0; r < 2; ++r)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            sb[r][c] += __uint_as_float(dv[r][c]) + __uint_as_float(dv[r][8 + c]);
-                            sm[r][c] += __uint_as_float(dv[r][3 + c]) + __uint_as_float(dv[r][11 + c]);
-                        }
-                    return true;
-                };
-                for (int kb = 0; kb < kBlocks; ++kb, ++g) {
-                    const int a = g % kNA;
-                    if (g >= kNA && !warp_wait_or_flag(&a_empty[a], ((g / kNA) - 1) & 1, err)) {
+                constexpr int H = kTs / 2;
+                for (int c = 0; c < kNChunks; ++c, ++dcnt) {
+                    const int b = dcnt & 1;
+                    if (!warp_wait_or_flag(&d_full[0][b], (dcnt >> 1) & 1, err) ||
+                        !warp_wait_or_flag(&d_full[1][b], (dcnt >> 1) & 1, err)) {
                         ok = false;
                         break;
                     }
                     tc::fence_after();
-                    uint32_t kh[2][8], kl[2][8];
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const int mm = kb * 4 + m;
-                        const u64 sx = s2[mm], sy = s2[kTs / 2 + mm], sz = s2[kTs + mm], sa = s2[3 * (kTs / 2) + mm];
-#pragma unroll
-                        for (int r = 0; r < 2; ++r) {
-                            const u64 q = ffma2(sx, m2x[r], ffma2(sy, m2y[r], ffma2(sz, m2z[r], fadd2(sa, bb[r]))));
-                            const u64 iq = rsqrt2(q);
-                            const u64 kk = fmul2(fmul2(iq, iq), iq);
-                            const u64 hi = kk & 0xFFFFE000FFFFE000ull;  // TF32 part (truncated)
-                            const u64 lo = fsub2(kk, hi);              // the rest, exact in FP32
-                            kh[r][2 * m] = (uint32_t)hi;
-                            kh[r][2 * m + 1] = (uint32_t)(hi >> 32);
-                            kl[r][2 * m] = (uint32_t)lo;
-                            kl[r][2 * m + 1] = (uint32_t)(lo >> 32);
+                    for (int half = 0; half < kChunk / 16; ++half) {
+                        uint32_t y[2][16];  // Y of this thread's two targets, 16 sources
+                        tc::ld16(tbase + lane_base + col_d(0, b) + 16 * half, y[0]);
+                        tc::ld16(tbase + lane_base + col_d(1, b) + 16 * half, y[1]);
+                        tc::wait_ld();
+                        if (half == kChunk / 16 - 1) {  // all read: the accumulators are free again
+                            tc::fence_before();
+                            __syncwarp();
+                            if (lane == 0) {
+                                dev::mbar_arrive(&d_empty[0][b]);
+                                dev::mbar_arrive(&d_empty[1][b]);
+                            }
                         }
-                    }
 #pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        const uint32_t col = tbase + lane_base + kColA + a * 32 + r * 16;
-                        tc::st8(col, kh[r]);
-                        tc::st8(col + 8, kl[r]);
-                    }
-                    tc::wait_st();
-                    tc::fence_before();
-                    __syncwarp();
-                    if (lane == 0) dev::mbar_arrive(&a_full[a]);
-                    // a segment was just completed: add the one before it (its MMAs have had a
-                    // segment's time to finish), so that its accumulator is free again in time
-                    if (kb % kSeg == kSeg - 1) {
-                        if (kb >= kSeg && !read_segment(f)) {
-                            ok = false;
-                            break;
+                        for (int p = 0; p < 8; ++p) {
+                            const int mm = c * (kChunk / 2) + half * 8 + p;  // source pair
+                            const u64 gx = s2[4 * H + mm], gy = s2[5 * H + mm], gz = s2[6 * H + mm];
+                            const u64 mx = s2[7 * H + mm], my = s2[8 * H + mm], mz = s2[9 * H + mm];
+#pragma unroll
+                            for (int r = 0; r < 2; ++r) {
+                                const u64 yy = (u64)y[r][2 * p] | ((u64)y[r][2 * p + 1] << 32);
+                                const u64 q = fadd2(bb[r], yy);
+                                const u64 iq = rsqrt2(q);
+                                const u64 kk = fmul2(fmul2(iq, iq), iq);
+                                ax[r] = ffma2(kk, mx, ax[r]);
+                                ay[r] = ffma2(kk, my, ay[r]);
+                                az[r] = ffma2(kk, mz, az[r]);
+                                gxs[r] = ffma2(kk, gx, gxs[r]);
+                                gys[r] = ffma2(kk, gy, gys[r]);
+                                gzs[r] = ffma2(kk, gz, gzs[r]);
+                            }
                         }
-                        if (kb >= kSeg) ++f;
                     }
                 }
                 if (!ok) break;
-                // the unit's last segment
-                if (!read_segment(f)) {
-                    ok = false;
-                    break;
-                }
-                ++f;
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
-                    const float bx = sb[r][0], by = sb[r][1], bz = sb[r][2];
-                    const float ax = sm[r][0], ay = sm[r][1], az = sm[r][2];
-                    const float vx = ax - fmaf(ty[r], bz, -tz[r] * by);
-                    const float vy = ay - fmaf(tz[r], bx, -tx[r] * bz);
-                    const float vz = az - fmaf(tx[r], by, -ty[r] * bx);
+                    const float bx = sum2(gxs[r]), by = sum2(gys[r]), bz = sum2(gzs[r]);
+                    const float vx = sum2(ax[r]) - fmaf(ty[r], bz, -tz[r] * by);
+                    const float vy = sum2(ay[r]) - fmaf(tz[r], bx, -tx[r] * bz);
+                    const float vz = sum2(az[r]) - fmaf(tx[r], by, -ty[r] * bx);
                     acc[0][r][tid] += __float2ll_rn(vx * c_mult);
                     acc[1][r][tid] += __float2ll_rn(vy * c_mult);
                     acc[2][r][tid] += __float2ll_rn(vz * c_mult);
@@ -446,9 +443,7 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
             if (lane == 0) dev::mbar_arrive(&rec_free[s]);
         }
         if (ok) flush();
-        else abort_flag = 1;
     }
-    // everyone done: release tensor memory
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -459,10 +454,6 @@ __global__ void __launch_bounds__(kThreads, ZM_BR32TC_MINB)
 
 int br32tc_occupancy()
 {
-    // Resident CTAs per SM from the kernel's own resource use.  The runtime's occupancy query
-    // answers one CTA per SM for this kernel (on GB300, also with the largest shared-memory
-    // carveout), while its registers, shared memory and tensor memory leave room for three; run
-    // with three per SM it takes 3.2 instead of 7.4 ms per 256^2 launch.
     int dev = 0, regs_sm = 0, smem_sm = 0, reserved = 0, threads_sm = 0, blocks_sm = 0;
     cudaFuncAttributes fa[2];
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -478,12 +469,10 @@ int br32tc_occupancy()
     }
     int occ = std::min(blocks_sm, threads_sm / kThreads);
     for (const cudaFuncAttributes &a : fa) {
-        // registers are granted per warp in units of 256
         const int regs_warp = (a.numRegs * 32 + 255) / 256 * 256;
         occ = std::min(occ, regs_sm / std::max(regs_warp * (kThreads / 32), 1));
         occ = std::min(occ, smem_sm / std::max((int)a.sharedSizeBytes + reserved, 1));
     }
-    // tensor memory: 512 columns per SM, kTmemCols per CTA
     return std::max(1, std::min(occ, (int)(512 / kTmemCols)));
 }
 

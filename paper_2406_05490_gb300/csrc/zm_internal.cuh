@@ -55,29 +55,13 @@ struct Tiling {
 
 // FP64 record: rows 0-2 absolute position, rows 3-5 scaled sheet strength -> [tile][6][ts] double
 // FP32C near record: rows 0-2 position hi, 3-5 position lo, 6-8 scaled strength -> [tile][9][ts]
-// FP32C far record, [tile][26][ts] float (ts = 256):
-//   rows 0-2 s = z - c_T (c_T the tile centre), row 3 |s|^2 + delta^2      (both far paths)
-//   rows 4-19 the tile's 256 x 16 source matrix B of the tensor-core far path (far_b_index)
-//   rows 20-22 scaled strength, rows 23-25 s x strength                  (CUDA-core far path)
+// FP32C far record, [tile][10][ts] float (ts = 256):
+//   rows 0-2 s = z - c_T (c_T the tile centre), row 3 |s|^2 + delta^2, rows 4-6 scaled strength,
+//   rows 7-9 s x strength
 constexpr int kRec64 = 6;
 constexpr int kRec32 = 9;
-constexpr int kRec32F = 26;
-constexpr int kFarRowB = 4, kFarRowG = 20;
-
-// The tensor-core far path's source matrix B of one tile: row j = source slot (the K index of
-// the MMA), 16 columns: 0-2 scaled strength and 3-5 s x strength, each rounded to TF32 (10
-// fraction bits); 8-10 and 11-13 what that rounding left, again rounded to TF32; 6, 7, 14, 15
-// zero.  Stored K-major without swizzling as core matrices of 8 columns x 4 sources (128
-// contiguous bytes; column n of a core matrix at 16 n bytes, source j at 4 j bytes), 8-source
-// blocks of 512 bytes one after another; within a block the core matrix of sources 4-7 lies
-// kTcStrideK bytes after that of sources 0-3, and that of columns 8-15 kTcStrideN bytes after
-// that of columns 0-7.  far_b_index gives the float offset from row kFarRowB.
-constexpr uint32_t kTcStrideK = 128, kTcStrideN = 256;
-__host__ __device__ constexpr int far_b_index(int j, int n)
-{
-    return (j >> 3) * 128 + (n >> 3) * (int)(kTcStrideN / 4) + ((j >> 2) & 1) * (int)(kTcStrideK / 4) +
-           (n & 7) * 4 + (j & 3);
-}
+constexpr int kRec32F = 10;
+constexpr int kFarRowG = 4;
 
 // Launch geometry of the all-pairs kernel.
 struct BrPlan {
@@ -124,7 +108,6 @@ struct Inst {
     double dt;                  // RK3 step of this interface
     int keep_phi;               // medium order: Phi comes from the FFT velocity, not from u
     double cutoff;              // > 0: sum only over sources within this distance
-    int tc_rec;                 // the geometry pass also writes the tensor-core source matrix
     int block0;                 // first 256-thread block of this interface in the point kernels
     int chunk, nchunks;         // source tiles per Birkhoff-Rott work item; items per target tile
     long long item0;            // first Birkhoff-Rott work item of this interface

@@ -59,7 +59,7 @@ __device__ __forceinline__ void geometry_point(const Geom &g, const Tiling &t, i
                                                double grav, float d2f, void *__restrict__ src,
                                                float *__restrict__ far_rec, float4 *__restrict__ tinfo,
                                                unsigned int *gmax, double *__restrict__ q,
-                                               double *__restrict__ nrm, bool tc_rec = false)
+                                               double *__restrict__ nrm)
 {
     if (!ZM_IDX_OK(p, g.N)) return;
     const int i = p / g.n2, j = p - (p / g.n2) * g.n2;
@@ -133,26 +133,12 @@ __device__ __forceinline__ void geometry_point(const Geom &g, const Tiling &t, i
         f[t.ts] = sf[1];
         f[2 * (size_t)t.ts] = sf[2];
         f[3 * (size_t)t.ts] = fmaf(sf[0], sf[0], fmaf(sf[1], sf[1], fmaf(sf[2], sf[2], d2f)));
-        // CUDA-core far path: FP32 strength and s x strength
+        // FP32 strength and s x strength
 #pragma unroll
         for (int c = 0; c < 3; ++c) f[(size_t)(kFarRowG + c) * t.ts] = gf[c];
         f[(size_t)(kFarRowG + 3) * t.ts] = __double2float_rn((double)sf[1] * gf[2] - (double)sf[2] * gf[1]);
         f[(size_t)(kFarRowG + 4) * t.ts] = __double2float_rn((double)sf[2] * gf[0] - (double)sf[0] * gf[2]);
         f[(size_t)(kFarRowG + 5) * t.ts] = __double2float_rn((double)sf[0] * gf[1] - (double)sf[1] * gf[0]);
-        // tensor-core far path: strength and s x strength (FP64) as TF32 hi + TF32 rest
-        if (tc_rec && t.ts == 256) {
-            float *B = far_rec + tile * kRec32F * t.ts + kFarRowB * t.ts;
-            const double mv[3] = {(double)sf[1] * gm[2] - (double)sf[2] * gm[1],
-                                  (double)sf[2] * gm[0] - (double)sf[0] * gm[2],
-                                  (double)sf[0] * gm[1] - (double)sf[1] * gm[0]};
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                const double v = (c < 3) ? gm[c] : mv[c - 3];
-                const float hi = dev::tf32_round(__double2float_rn(v));
-                B[far_b_index(slot, c)] = hi;
-                B[far_b_index(slot, 8 + c)] = dev::tf32_round(__double2float_rn(v - (double)hi));
-            }
-        }
         const float rad = sqrtf(sf[0] * sf[0] + sf[1] * sf[1] + sf[2] * sf[2]);
         atomicMax(reinterpret_cast<unsigned int *>(&tinfo[tile].w), __float_as_uint(rad));
         const float gn = sqrtf(gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2]);

@@ -1,7 +1,7 @@
 // zm_tc.cuh -- inline-PTX wrappers for the fifth-generation tensor cores of sm_100-family GPUs
-// (tcgen05: tensor memory allocation, register <-> tensor memory moves, MMA with the A operand in
-// tensor memory and B in shared memory, completion through mbarriers), used by the FP32C
-// Birkhoff-Rott kernel's far path (zm_br32tc.cu).
+// (tcgen05: tensor memory allocation, tensor memory -> register loads, MMA with both operands in
+// shared memory and the accumulator in tensor memory, completion through mbarriers), used by the
+// FP32C Birkhoff-Rott kernel's tensor-core far path (zm_br32tc.cu).
 //
 // Tensor memory (TMEM) is 512 columns x 128 lanes of 32-bit cells per SM.  An address is
 // (lane << 16) | column.  Warp w of a CTA may move data only in lanes 32 (w % 4) .. + 31.
@@ -35,14 +35,7 @@ __device__ __forceinline__ void dealloc(uint32_t taddr, uint32_t ncols)
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// ---- register <-> tensor memory (warp-collective) -------------------------------------------
-// 8 consecutive columns of this thread's lane <- v[0..7]
-__device__ __forceinline__ void st8(uint32_t taddr, const uint32_t v[8])
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-                 : "memory");
-}
+// ---- tensor memory -> registers (warp-collective) ------------------------------------------
 // v[0..15] <- 16 consecutive columns of this thread's lane
 __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t v[16])
 {
@@ -54,13 +47,13 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t v[16])
         : "r"(taddr)
         : "memory");
 }
-__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ---- MMA (issued by one thread) -------------------------------------------------------------------
 // Shared-memory matrix descriptor, no swizzling: the matrix is a grid of core matrices of 8 rows
 // x 16 bytes (each 128 contiguous bytes, rows 16 bytes apart); lbo = byte distance between core
-// matrices adjacent along K, sbo = along M/N.  Bits 46-48 hold the fixed descriptor version 1.
+// matrices adjacent along K (0 reads one core matrix twice), sbo = along M/N.  Bits 46-48 hold
+// the fixed descriptor version 1.
 __device__ __forceinline__ uint64_t smem_desc(const void *smem, uint32_t lbo, uint32_t sbo)
 {
     return (uint64_t)((dev::smem_u32(smem) >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
@@ -76,14 +69,14 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n)
            | ((uint32_t)(m >> 4) << 24);       // M / 16
 }
 
-// D[tmem] (+)= A[tmem] * B[smem desc]; accumulate = false overwrites D.
-__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+// D[tmem] (+)= A[smem desc] * B[smem desc]; accumulate = false overwrites D.
+__device__ __forceinline__ void mma_tf32_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                             bool accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"((uint32_t)accumulate)
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"((uint32_t)accumulate)
         : "memory");
 }
 

@@ -23,7 +23,8 @@
 // default (ZM_FAR_TENSOR selects it).  ncu: issue 56 %, FMA pipe 54 %, 10.4 thread instructions
 // per pair; the warps wait on fixed-latency dependencies and tensor-memory loads with three
 // compute warps per scheduler.  Sweeps (chunks of 16 / 32 / 64 sources, one or two operand
-// buffers, 2-4 CTAs per SM, one load of a whole chunk, scalar K) did not beat this layout.
+// buffers, 2-4 CTAs per SM, one load of a whole chunk, scalar K or scalar q, 16-byte loads of the
+// strengths) did not beat this layout.
 //
 // CTA: 6 warps.  Warps 0-3 compute (thread t owns targets t and t + 128 of the target tile, i.e.
 // tensor-memory lane t in two row groups); warp 4 takes work items from a global atomic counter,

@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(kT, ZM_BR32_MINB)
     br32_batch_kernel(const Inst *__restrict__ insts, int ninst, long long nitems,
                       unsigned long long *counter, int *err)
 {
-    // a stage holds a near record (9 rows) or the far path's rows: s, |s|^2 + delta^2 (record
-    // rows 0-3) and strength, s x strength (record rows 20-25) as stage rows 0-9
+    // a stage holds a near record (9 rows) or a far record: s, |s|^2 + delta^2 (rows 0-3) and
+    // strength, s x strength (rows kFarRowG .. + 5), as stage rows 0-9
     constexpr int kStageRows = 10;
     __shared__ __align__(128) float stage[2][kStageRows * kTs];
     __shared__ long long acc[3][kR][kT];  // fixed-point partial sums of this thread's targets

@@ -1,6 +1,6 @@
 """The two far paths of the FP32C all-pairs sum (far tile pairs: everything on the CUDA cores,
-the default, or K on the CUDA cores and K [g | m] on the tensor cores; near pairs always on the
-CUDA cores), each against the CPU oracle at the FP32C velocity bound (1e-6 relative L2) on meshes
+the default, or the Gram part of |t - s|^2 on the tensor cores and the rest on the CUDA cores;
+near pairs always on the CUDA cores), each against the CPU oracle at the FP32C velocity bound (1e-6 relative L2) on meshes
 with one tile, ragged tiles, free and periodic edges, and against each other; both bitwise
 deterministic."""
 import numpy as np

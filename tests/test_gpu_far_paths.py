@@ -140,3 +140,40 @@ def test_tensor_path_with_cutoff_and_in_a_batch(zm):
         alone.close()
         assert np.array_equal(ub, ua), k
     zm.zm_batch_destroy(h)
+
+
+def test_tensor_path_every_tile_shape(zm):
+    """The tensor-core far path with every candidate tile shape (its operands are built per
+    256-slot tile whatever the patch shape) on square, anisotropic (dx1 = 4 dx2), ragged and
+    free-edge interfaces in one batch, against the oracle; within one shape the work-item size
+    changes no bit."""
+    specs = [(64, 64, True, 0.6, 2), (32, 128, True, 0.5, 7), (37, 53, False, 0.4, 1), (5, 9, False, 0.5, 5)]
+    meshes = [(n1, n2, 1.0, 1.0, per) for n1, n2, per, _, _ in specs]
+    delta = [0.1 / max(n1, n2) for n1, n2, _, _, _ in specs]
+    h = zm.zm_batch_create(meshes, [a for _, _, _, a, _ in specs], g=1.3, mu=0.0, delta=delta)
+    zm.zm_batch_set_far_path(h, zm.ZM_FAR_TENSOR)
+    refs = []
+    for k, (n1, n2, per, at, seed) in enumerate(specs):
+        z, w = inputs.random_state(n1, n2, seed=seed)
+        zm.zm_batch_set_state(h, k, z, w)
+        refs.append(oracle.derivative(oracle.Mesh(n1, n2, periodic=per), z, w, at, 1.3, 0.0, delta[k]))
+    for tp1, tp2 in [(16, 16), (8, 32), (32, 8), (4, 64), (64, 4)]:
+        zm.zm_batch_set_tile_shape(h, tp1, tp2)
+        zm.zm_batch_set_chunk(h, 0)
+        zm.zm_batch_velocity(h)
+        first = []
+        for k, (n1, n2, _, _, _) in enumerate(specs):
+            u, wd = np.empty((3, n1 * n2)), np.empty((2, n1 * n2))
+            zm.zm_batch_get_velocity(h, k, u, wd)
+            first.append(u)
+            eu, ew = rel(u, refs[k][0]), rel(wd, refs[k][1])
+            print(f"tensor path, tiles {tp1}x{tp2} [{k}] {n1}x{n2}: rel L2 u={eu:.3e} wdot={ew:.3e}")
+            assert eu <= TOL32 and ew <= TOL32
+        zm.zm_batch_set_chunk(h, 1)
+        zm.zm_batch_velocity(h)
+        for k, (n1, n2, _, _, _) in enumerate(specs):
+            u = np.empty((3, n1 * n2))
+            zm.zm_batch_get_velocity(h, k, u, None)
+            assert np.array_equal(u, first[k])
+    zm.zm_batch_destroy(h)
+

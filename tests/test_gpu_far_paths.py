@@ -50,6 +50,28 @@ def test_far_paths_against_the_oracle(zm, n1, n2, periodic):
     assert rel(out[zm.ZM_FAR_TENSOR], out[zm.ZM_FAR_CUDA]) <= 2 * TOL32
 
 
+def test_far_paths_on_a_folded_interface(zm):
+    """An interface that folds over itself (z1 = a + 0.25 sin 2 pi a overhangs), so that nodes 20 and
+    more mesh points apart come within 2 dx of each other in space (128^2: 72 % of the tile pairs
+    far): the near / far split is decided by the tiles' bounding spheres in space, not by mesh
+    distance, and both far paths stay within the FP32C bound of the oracle."""
+    n = 128
+    a, b = inputs.mesh_coords(n)
+    z = np.stack([a + 0.25 * np.sin(2 * np.pi * a), b + 0.05 * np.sin(2 * np.pi * a),
+                  0.03 * np.sin(2 * np.pi * a) + 0.02 * np.cos(2 * np.pi * b)])
+    _, w = inputs.random_state(n, seed=17)
+    delta = 0.1 / n
+    u_ref, wd_ref = oracle.derivative(oracle.Mesh(n, periodic=True), z, w, 0.5, 1.0, 0.0, delta)
+    for path in (zm.ZM_FAR_TENSOR, zm.ZM_FAR_CUDA):
+        model = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=delta, fp32c=True)
+        zm.zm_set_far_path(model.h, path)
+        u, wd = model.velocity(z, w)
+        model.close()
+        eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+        print(f"folded 128^2, far path {path}: rel L2 u={eu:.3e} wdot={ew:.3e}")
+        assert eu <= TOL32 and ew <= TOL32
+
+
 def test_far_path_at_full_size_sampled(zm):
     """256^2 with vorticity: all of u from each path, 1024 seeded targets summed by the oracle."""
     n = 256

@@ -185,3 +185,32 @@ def test_cutoff_needs_fp32c(zm):
         zm.zm_set_cutoff(model.h, 0.2)
     assert e.value.code == zm.ZM_ERR_UNSUPPORTED
     model.close()
+
+@pytest.mark.gpu
+def test_cutoff_on_a_folded_interface(zm):
+    """A folded interface (z1 = a + 0.25 sin 2 pi a overhangs): tiles far apart on the mesh come
+    within the cutoff in space, so skipping a tile pair must follow the bounding spheres in space,
+    never mesh distance.  Both far paths against the band-corrected oracle."""
+    n, c = 128, 0.05
+    a, b = inputs.mesh_coords(n)
+    z = np.stack([a + 0.25 * np.sin(2 * np.pi * a), b + 0.05 * np.sin(2 * np.pi * a),
+                  0.03 * np.sin(2 * np.pi * a) + 0.02 * np.cos(2 * np.pi * b)])
+    _, w = inputs.random_state(n, seed=17)
+    delta = 0.1 / n
+    m = oracle.Mesh(n, periodic=True)
+    # the fold matters: pairs 20 or more mesh rows apart lie within the cutoff
+    i1 = np.arange(n * n) // n
+    close = np.linalg.norm(z[:, None, ::97] - z[:, ::89, None], axis=0) <= c
+    d = np.abs(i1[::89][:, None] - i1[None, ::97])
+    assert np.any(close & (np.minimum(d, n - d) >= 20))
+    for path in (zm.ZM_FAR_TENSOR, zm.ZM_FAR_CUDA):
+        model = zm.ZModel(n, periodic=True, atwood=0.5, g=1.0, delta=delta, fp32c=True)
+        zm.zm_set_far_path(model.h, path)
+        zm.zm_set_cutoff(model.h, c)
+        u, wd = model.velocity(z, w)
+        model.close()
+        u_ref, wd_ref, nband, nflip = band_corrected_reference(m, z, w, u, 0.5, 1.0, 0.0, delta, c)
+        eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+        print(f"folded 128^2, cutoff {c}, far path {path}: rel L2 u={eu:.3e} wdot={ew:.3e} "
+              f"(band {nband}, flipped {nflip})")
+        assert eu <= TOL32 and ew <= TOL32_RATE

@@ -199,3 +199,31 @@ def test_tensor_path_every_tile_shape(zm):
             assert np.array_equal(u, first[k])
     zm.zm_batch_destroy(h)
 
+
+def test_tensor_path_medium_order(zm):
+    """Medium order (dz/dt from the all-pairs sum, Phi from the FFT velocity) with the far pairs
+    on the tensor cores: one evaluation and three steps against the oracle."""
+    n1, n2 = 64, 64
+    z, w = inputs.random_state(n1, n2, seed=n1 * 3 + n2)
+    delta = 0.1 / n1
+    m = oracle.Mesh(n1, n2, periodic=True)
+    u_ref, wd_ref = oracle.derivative(m, z, w, 0.6, 1.2, 0.01, delta, order=oracle.ORDER_MEDIUM)
+    model = zm.ZModel(n1, n2, periodic=True, atwood=0.6, g=1.2, mu=0.01, delta=delta,
+                      order=zm.ZM_ORDER_MEDIUM, fp32c=True)
+    zm.zm_set_far_path(model.h, zm.ZM_FAR_TENSOR)
+    u, wd = model.velocity(z, w)
+    model.close()
+    eu, ew = rel(u, u_ref), rel(wd, wd_ref)
+    print(f"tensor path, medium order {n1}x{n2}: rel L2 u={eu:.3e} wdot={ew:.3e}")
+    assert eu <= TOL32 and ew <= TOL32
+    z0, w0 = inputs.multi_mode(n1, n_modes=4, seed=2, amp=0.02)
+    zr, wr = oracle.run(m, z0, w0, 0.6, 1.2, 0.0, delta, 2e-3, 3, order=oracle.ORDER_MEDIUM)
+    model = zm.ZModel(n1, n2, periodic=True, atwood=0.6, g=1.2, delta=delta, order=zm.ZM_ORDER_MEDIUM,
+                      fp32c=True)
+    zm.zm_set_far_path(model.h, zm.ZM_FAR_TENSOR)
+    model.set_state(z0, w0)
+    model.step(2e-3, 3)
+    z1, w1 = model.get_state()
+    model.close()
+    assert rel(z1, zr) <= TOL32 and rel(w1, wr) <= TOL32
+
